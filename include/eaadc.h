@@ -1,0 +1,135 @@
+/*
+ * eaadc.h - C ABI of the GB300 (sm_103a) DF-EA-ADC(3) sigma/Davidson library.
+ *
+ * Method: non-Dyson EA-ADC(n) in the intermediate-state representation
+ * (arXiv:2511.05897, Sec. II.A, Eq. 1-6), truncated by perturbation order
+ * (Eq. 5), with density-fitted integrals (pq|rs) = sum_Q B^Q_pq B^Q_rs
+ * (Sec. II.B, Eq. 25), state-specific frozen natural orbitals (Sec. II.C,
+ * Eq. 9-17), natural auxiliary functions (Sec. II.D, Eq. 27-29) and the
+ * perturbative truncation correction (Sec. II.E, Eq. 30).  The secular matrix
+ * M is diagonalised by Davidson's method from sigma vectors sigma = M c
+ * (Sec. II.A, last paragraph).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an eaadc_status and never aborts; on failure
+ *    eaadc_last_error(ctx) holds a one-line message (valid until the next call
+ *    on that context).
+ *  - Host arrays are owned by the caller and only read (or written, for
+ *    outputs) during the call.
+ *  - Device buffers passed to eaadc_sigma are owned by the caller; all other
+ *    device memory is owned by the context and freed by eaadc_destroy.
+ *  - A context is bound to one CUDA device; calls on one context must not run
+ *    concurrently (thread-compatible, not thread-safe).
+ *  - Vector layout of one attached-state vector of state s (dimension
+ *    dim = v' + o*v'*v'): [1p part y[a], a < v'] followed by the 2p1h part
+ *    w[k][b][c] (k < o, b, c < v', c fastest) in the orthonormal doublet
+ *    representation: sym(w) in (b,c) is the pair-singlet and antisym(w) the
+ *    pair-triplet coupled doublet, so M is symmetric.
+ *  - Energies are in hartree; attachment energies omega, EA = -omega.
+ */
+#ifndef EAADC_H
+#define EAADC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eaadc_ctx eaadc_ctx;
+
+typedef enum {
+  EAADC_OK = 0,
+  EAADC_ERR_ARG = -1,       /* invalid argument (sizes, pointers, state index) */
+  EAADC_ERR_ALLOC = -2,     /* device or host allocation failed */
+  EAADC_ERR_CUDA = -3,      /* a CUDA runtime call or kernel failed */
+  EAADC_ERR_NOCONV = -4,    /* Davidson reached maxit without convergence */
+  EAADC_ERR_NONFINITE = -5, /* NaN/Inf in an input, sigma or residual */
+  EAADC_ERR_TIMEOUT = -6,   /* a bounded device wait expired */
+  EAADC_ERR_STATE = -7      /* call out of order (e.g. sigma before build) */
+} eaadc_status;
+
+typedef enum {
+  EAADC_FP64 = 0,        /* every operation in FP64 */
+  EAADC_MIXED_BF16 = 1   /* DF ladder and ring GEMMs on tcgen05 tensor cores:
+                            BF16 operands, FP32 accumulation; rest FP64 */
+} eaadc_prec;
+
+typedef struct {
+  double tol;     /* converged when every residual 2-norm <= tol ... */
+  double etol;    /* ... and every Ritz value moved by <= etol */
+  int maxit;      /* iteration limit */
+  int max_sub;    /* subspace size limit per state (<= 96) */
+  int prec;       /* eaadc_prec used for the sigma vectors inside the loop */
+  int refine;     /* 1: after a mixed-precision solve, FP64 sigma of the Ritz
+                     vectors and FP64 Rayleigh-Ritz, then FP64 Davidson
+                     iterations until tol is met in FP64 */
+} eaadc_davidson_opts;
+
+/* Library version string (static storage). */
+const char* eaadc_version(void);
+
+/* Create a context on `device` and upload the canonical problem.
+ *  o, v, naux : occupied, virtual and auxiliary sizes (o >= 1, v >= 1, naux >= 1)
+ *  eps_occ    : host [o] occupied orbital energies
+ *  eps_vir    : host [v] virtual orbital energies
+ *  B          : host [naux][o+v][o+v] row-major DF factor B^Q_pq in the MO
+ *               basis (the paper's J^Q_pq of Eq. 26), symmetric in (p,q);
+ *               only the oo, ov and vv blocks are read.
+ *  stream     : cudaStream_t used for all internal work (NULL = legacy default)
+ * Eq. 25 defines (pq|rs) from B.  On success *out owns device copies. */
+eaadc_status eaadc_init(eaadc_ctx** out, int o, int v, int naux,
+                        const double* eps_occ, const double* eps_vir, const double* B,
+                        int device, void* stream);
+
+/* Build one untruncated (canonical) state: state 0 uses the full virtual and
+ * auxiliary spaces.  adc_order is 2 or 3; x3 scales the third-order 1p/1p
+ * block (1.0 = ADC(3)).  Computes the first-order amplitudes, the 1p/1p block
+ * through order adc_order and the stored (oo|vv) and (ov|ov) integrals. */
+eaadc_status eaadc_build_canonical(eaadc_ctx* ctx, int adc_order, double x3);
+
+/* Number of built states and the dimensions of state s. */
+eaadc_status eaadc_state_info(const eaadc_ctx* ctx, int state, int* vprime, int* nauxprime,
+                              long long* dim);
+
+/* sigma = M x for nvec vectors of state `state`.
+ *  x_dev, sigma_dev : caller-owned device buffers [nvec][dim] (FP64), must not
+ *                     overlap; used on `stream` (cudaStream_t, NULL = legacy).
+ *  prec             : eaadc_prec. */
+eaadc_status eaadc_sigma(eaadc_ctx* ctx, int state, int nvec, const double* x_dev,
+                         double* sigma_dev, int prec, void* stream);
+
+/* Same as eaadc_sigma with host buffers [nvec][dim]; includes the copies. */
+eaadc_status eaadc_sigma_host(eaadc_ctx* ctx, int state, int nvec, const double* x_host,
+                              double* sigma_host, int prec);
+
+/* Davidson diagonal preconditioner values D (host [dim]): D_a = M_aa for the
+ * 1p part, e_b + e_c - e_k for the 2p1h part. */
+eaadc_status eaadc_diagonal(eaadc_ctx* ctx, int state, double* diag_host);
+
+/* Copy the 1p/1p block M_ab of a state to host [v'][v']. */
+eaadc_status eaadc_get_m11(eaadc_ctx* ctx, int state, double* m11_host);
+
+/* Lowest nroots roots of every built state by Davidson.
+ *  omega   : host [nstates][nroots] Ritz values (hartree)
+ *  resnorm : host [nstates][nroots] final residual 2-norms (may be NULL)
+ *  iters   : host [nstates] iterations used (may be NULL)
+ * Returns EAADC_ERR_NOCONV (with results filled) if maxit was reached. */
+eaadc_status eaadc_davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts* opts,
+                            double* omega, double* resnorm, int* iters);
+
+/* Converged eigenvectors of state s from the last eaadc_davidson, host
+ * [nroots][dim]. */
+eaadc_status eaadc_get_eigvecs(eaadc_ctx* ctx, int state, double* vec_host);
+
+/* Free everything owned by the context (NULL is ignored). */
+void eaadc_destroy(eaadc_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none); static for ctx==NULL. */
+const char* eaadc_last_error(const eaadc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EAADC_H */

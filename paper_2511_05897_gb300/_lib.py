@@ -1,0 +1,165 @@
+"""ctypes binding of libeaadc.so: the C entry points of include/eaadc.h under
+the same names.  Argument marshalling only: every computation runs in the
+CUDA library, and loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libeaadc.so")
+
+EAADC_OK = 0
+EAADC_ERR_ARG = -1
+EAADC_ERR_ALLOC = -2
+EAADC_ERR_CUDA = -3
+EAADC_ERR_NOCONV = -4
+EAADC_ERR_NONFINITE = -5
+EAADC_ERR_TIMEOUT = -6
+EAADC_ERR_STATE = -7
+EAADC_FP64 = 0
+EAADC_MIXED_BF16 = 1
+
+EXPORTED = (
+    "eaadc_version", "eaadc_init", "eaadc_build_canonical", "eaadc_state_info", "eaadc_sigma",
+    "eaadc_sigma_host", "eaadc_diagonal", "eaadc_get_m11", "eaadc_davidson", "eaadc_get_eigvecs",
+    "eaadc_destroy", "eaadc_last_error",
+)
+
+
+class EaadcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"eaadc status {status}: {msg}")
+        self.status = status
+
+
+class DavidsonOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("etol", C.c_double), ("maxit", C.c_int), ("max_sub", C.c_int),
+                ("prec", C.c_int), ("refine", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.eaadc_version.restype = C.c_char_p
+        L.eaadc_init.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, vp]
+        L.eaadc_build_canonical.argtypes = [vp, C.c_int, C.c_double]
+        L.eaadc_state_info.argtypes = [vp, C.c_int, ip, ip, C.POINTER(C.c_longlong)]
+        L.eaadc_sigma.argtypes = [vp, C.c_int, C.c_int, vp, vp, C.c_int, vp]
+        L.eaadc_sigma_host.argtypes = [vp, C.c_int, C.c_int, dp, dp, C.c_int]
+        L.eaadc_diagonal.argtypes = [vp, C.c_int, dp]
+        L.eaadc_get_m11.argtypes = [vp, C.c_int, dp]
+        L.eaadc_davidson.argtypes = [vp, C.c_int, C.POINTER(DavidsonOpts), dp, dp, ip]
+        L.eaadc_get_eigvecs.argtypes = [vp, C.c_int, dp]
+        L.eaadc_destroy.argtypes = [vp]
+        L.eaadc_destroy.restype = None
+        L.eaadc_last_error.argtypes = [vp]
+        L.eaadc_last_error.restype = C.c_char_p
+        for name in EXPORTED:
+            if name not in ("eaadc_version", "eaadc_destroy", "eaadc_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(ctx, st):
+    if st != EAADC_OK:
+        raise EaadcError(st, lib().eaadc_last_error(ctx).decode())
+
+
+def eaadc_version():
+    return lib().eaadc_version().decode()
+
+
+def eaadc_last_error(ctx):
+    return lib().eaadc_last_error(ctx).decode()
+
+
+def eaadc_init(o, v, naux, eps_occ, eps_vir, B, device=0, stream=None):
+    eo, ev, Bf = _f64(eps_occ), _f64(eps_vir), _f64(B)
+    if eo.size != o or ev.size != v or Bf.size != naux * (o + v) ** 2:
+        raise ValueError("array sizes do not match (o, v, naux)")
+    ctx = C.c_void_p()
+    st = lib().eaadc_init(C.byref(ctx), o, v, naux, _dp(eo), _dp(ev), _dp(Bf), device, stream)
+    _check(None, st)
+    return ctx
+
+
+def eaadc_build_canonical(ctx, adc_order=3, x3=1.0):
+    _check(ctx, lib().eaadc_build_canonical(ctx, adc_order, x3))
+
+
+def eaadc_state_info(ctx, state=0):
+    vp, npx, dim = C.c_int(), C.c_int(), C.c_longlong()
+    _check(ctx, lib().eaadc_state_info(ctx, state, C.byref(vp), C.byref(npx), C.byref(dim)))
+    return vp.value, npx.value, dim.value
+
+
+def eaadc_sigma(ctx, state, nvec, x_ptr, sigma_ptr, prec=EAADC_FP64, stream=None):
+    """Device pointers (ints, e.g. torch.Tensor.data_ptr()) of [nvec][dim] float64 buffers."""
+    _check(ctx, lib().eaadc_sigma(ctx, state, nvec, C.c_void_p(x_ptr), C.c_void_p(sigma_ptr), prec, stream))
+
+
+def eaadc_sigma_host(ctx, state, x, prec=EAADC_FP64):
+    x = _f64(x)
+    nvec = 1 if x.ndim == 1 else x.shape[0]
+    y = np.empty_like(x)
+    _check(ctx, lib().eaadc_sigma_host(ctx, state, nvec, _dp(x), _dp(y), prec))
+    return y
+
+
+def eaadc_diagonal(ctx, state=0):
+    dim = eaadc_state_info(ctx, state)[2]
+    out = np.empty(dim)
+    _check(ctx, lib().eaadc_diagonal(ctx, state, _dp(out)))
+    return out
+
+
+def eaadc_get_m11(ctx, state=0):
+    v = eaadc_state_info(ctx, state)[0]
+    out = np.empty((v, v))
+    _check(ctx, lib().eaadc_get_m11(ctx, state, _dp(out)))
+    return out
+
+
+def eaadc_davidson(ctx, nroots, nstates=1, tol=1e-6, etol=1e-10, maxit=200, max_sub=40, prec=EAADC_FP64,
+                   refine=1):
+    """Returns (omega[nstates, nroots], resnorm[nstates, nroots], iters[nstates], status)."""
+    opts = DavidsonOpts(tol, etol, maxit, max_sub, prec, refine)
+    om = np.zeros((nstates, nroots))
+    rn = np.zeros((nstates, nroots))
+    it = np.zeros(nstates, dtype=np.int32)
+    st = lib().eaadc_davidson(ctx, nroots, C.byref(opts), _dp(om), _dp(rn),
+                              it.ctypes.data_as(C.POINTER(C.c_int)))
+    if st not in (EAADC_OK, EAADC_ERR_NOCONV):
+        _check(ctx, st)
+    return om, rn, it, st
+
+
+def eaadc_get_eigvecs(ctx, state, nroots):
+    dim = eaadc_state_info(ctx, state)[2]
+    out = np.empty((nroots, dim))
+    _check(ctx, lib().eaadc_get_eigvecs(ctx, state, _dp(out)))
+    return out
+
+
+def eaadc_destroy(ctx):
+    lib().eaadc_destroy(ctx)

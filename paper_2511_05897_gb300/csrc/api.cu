@@ -1,0 +1,242 @@
+// extern "C" entry points; every call converts internal errors to a status
+// and a message (see include/eaadc.h for the contract of each function).
+#include "internal.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+eaadc_ctx::~eaadc_ctx() {
+  for (auto* s : states) delete s;
+  states.clear();
+}
+
+namespace {
+thread_local std::string g_static_err;
+
+template <class F>
+eaadc_status guarded(eaadc_ctx* ctx, F&& f) {
+  try {
+    if (ctx) ctx->err.clear();
+    f();
+    return EAADC_OK;
+  } catch (const ea::Error& e) {
+    if (ctx) ctx->err = e.msg; else g_static_err = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->err = "host allocation failed"; else g_static_err = "host allocation failed";
+    return EAADC_ERR_ALLOC;
+  } catch (...) {
+    if (ctx) ctx->err = "unknown internal error"; else g_static_err = "unknown internal error";
+    return EAADC_ERR_STATE;
+  }
+}
+
+void set_device(const eaadc_ctx* ctx) { EA_CK(cudaSetDevice(ctx->device)); }
+
+ea::State& get_state(eaadc_ctx* ctx, int s) {
+  if (s < 0 || s >= (int)ctx->states.size()) ea::fail(EAADC_ERR_ARG, "state index out of range (build states first)");
+  return *ctx->states[s];
+}
+
+bool all_finite(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
+const char* eaadc_version(void) { return "eaadc-gb300 0.1 (sm_103a)"; }
+
+eaadc_status eaadc_init(eaadc_ctx** out, int o, int v, int naux, const double* eps_occ, const double* eps_vir,
+                        const double* B, int device, void* stream) {
+  if (!out) { g_static_err = "out is NULL"; return EAADC_ERR_ARG; }
+  *out = nullptr;
+  if (o < 1 || v < 1 || naux < 1 || !eps_occ || !eps_vir || !B) {
+    g_static_err = "invalid sizes or NULL input";
+    return EAADC_ERR_ARG;
+  }
+  eaadc_ctx* ctx = new (std::nothrow) eaadc_ctx();
+  if (!ctx) { g_static_err = "host allocation failed"; return EAADC_ERR_ALLOC; }
+  eaadc_status st = guarded(ctx, [&] {
+    const int n = o + v;
+    if (!all_finite(eps_occ, o) || !all_finite(eps_vir, v)) ea::fail(EAADC_ERR_NONFINITE, "non-finite orbital energy");
+    int ndev = 0;
+    EA_CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) ea::fail(EAADC_ERR_ARG, "device index out of range");
+    ctx->device = device;
+    EA_CK(cudaSetDevice(device));
+    ctx->stream = (cudaStream_t)stream;
+    ctx->o = o; ctx->v = v; ctx->naux = naux;
+    cudaStream_t s = ctx->stream;
+    ctx->eo.alloc(o, s);
+    ctx->ev.alloc(v, s);
+    EA_CK(cudaMemcpyAsync(ctx->eo.p, eps_occ, sizeof(double) * o, cudaMemcpyHostToDevice, s));
+    EA_CK(cudaMemcpyAsync(ctx->ev.p, eps_vir, sizeof(double) * v, cudaMemcpyHostToDevice, s));
+    ctx->Boo.alloc((size_t)naux * o * o, s);
+    ctx->Bov.alloc((size_t)naux * o * v, s);
+    ctx->Bvv.alloc((size_t)naux * v * v, s);
+    const size_t nn = (size_t)n * n;
+    for (int Q = 0; Q < naux; ++Q) {
+      const double* BQ = B + (size_t)Q * nn;
+      EA_CK(cudaMemcpy2DAsync(ctx->Boo.p + (size_t)Q * o * o, sizeof(double) * o, BQ, sizeof(double) * n,
+                              sizeof(double) * o, o, cudaMemcpyHostToDevice, s));
+      EA_CK(cudaMemcpy2DAsync(ctx->Bov.p + (size_t)Q * o * v, sizeof(double) * v, BQ + o, sizeof(double) * n,
+                              sizeof(double) * v, o, cudaMemcpyHostToDevice, s));
+      EA_CK(cudaMemcpy2DAsync(ctx->Bvv.p + (size_t)Q * v * v, sizeof(double) * v, BQ + (size_t)o * n + o,
+                              sizeof(double) * n, sizeof(double) * v, v, cudaMemcpyHostToDevice, s));
+    }
+    EA_CK(cudaStreamSynchronize(s));
+  });
+  if (st != EAADC_OK) {
+    g_static_err = ctx->err;
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return EAADC_OK;
+}
+
+eaadc_status eaadc_build_canonical(eaadc_ctx* ctx, int adc_order, double x3) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    if (adc_order != 2 && adc_order != 3) ea::fail(EAADC_ERR_ARG, "adc_order must be 2 or 3");
+    if (!std::isfinite(x3)) ea::fail(EAADC_ERR_ARG, "x3 must be finite");
+    set_device(ctx);
+    cudaStream_t s = ctx->stream;
+    for (auto* p : ctx->states) delete p;
+    ctx->states.clear();
+    auto* st = new ea::State();
+    ctx->states.push_back(st);
+    st->o = ctx->o; st->v = ctx->v; st->naux = ctx->naux;
+    st->order = adc_order; st->x3 = x3;
+    const int o = ctx->o, v = ctx->v, naux = ctx->naux;
+    st->eo.alloc(o, s); st->ev.alloc(v, s);
+    st->Boo.alloc((size_t)naux * o * o, s);
+    st->Bov.alloc((size_t)naux * o * v, s);
+    st->Bvv.alloc((size_t)naux * v * v, s);
+    EA_CK(cudaMemcpyAsync(st->eo.p, ctx->eo.p, sizeof(double) * o, cudaMemcpyDeviceToDevice, s));
+    EA_CK(cudaMemcpyAsync(st->ev.p, ctx->ev.p, sizeof(double) * v, cudaMemcpyDeviceToDevice, s));
+    EA_CK(cudaMemcpyAsync(st->Boo.p, ctx->Boo.p, sizeof(double) * st->Boo.n, cudaMemcpyDeviceToDevice, s));
+    EA_CK(cudaMemcpyAsync(st->Bov.p, ctx->Bov.p, sizeof(double) * st->Bov.n, cudaMemcpyDeviceToDevice, s));
+    EA_CK(cudaMemcpyAsync(st->Bvv.p, ctx->Bvv.p, sizeof(double) * st->Bvv.n, cudaMemcpyDeviceToDevice, s));
+    ea::build_state_intermediates(ctx, *st);
+  });
+}
+
+eaadc_status eaadc_state_info(const eaadc_ctx* ctx, int state, int* vprime, int* nauxprime, long long* dim) {
+  if (!ctx) return EAADC_ERR_ARG;
+  if (state < 0 || state >= (int)ctx->states.size()) return EAADC_ERR_ARG;
+  const ea::State& st = *ctx->states[state];
+  if (vprime) *vprime = st.v;
+  if (nauxprime) *nauxprime = st.naux;
+  if (dim) *dim = st.dim;
+  return EAADC_OK;
+}
+
+eaadc_status eaadc_sigma(eaadc_ctx* ctx, int state, int nvec, const double* x_dev, double* sigma_dev, int prec,
+                         void* stream) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    ea::State& st = get_state(ctx, state);
+    if (nvec < 0 || (nvec > 0 && (!x_dev || !sigma_dev))) ea::fail(EAADC_ERR_ARG, "bad vector arguments");
+    if (prec != EAADC_FP64 && prec != EAADC_MIXED_BF16) ea::fail(EAADC_ERR_ARG, "unknown precision");
+    if (nvec == 0) return;
+    const char* xa = (const char*)x_dev;
+    const char* ya = (const char*)sigma_dev;
+    size_t bytes = sizeof(double) * (size_t)nvec * st.dim;
+    if (xa < ya + bytes && ya < xa + bytes) ea::fail(EAADC_ERR_ARG, "x and sigma overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (prec == EAADC_FP64) ea::sigma_fp64(s, st, nvec, x_dev, sigma_dev);
+    else ea::sigma_mixed(s, st, nvec, x_dev, sigma_dev);
+  });
+}
+
+eaadc_status eaadc_sigma_host(eaadc_ctx* ctx, int state, int nvec, const double* x_host, double* sigma_host,
+                              int prec) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    ea::State& st = get_state(ctx, state);
+    if (nvec <= 0 || !x_host || !sigma_host) ea::fail(EAADC_ERR_ARG, "bad vector arguments");
+    cudaStream_t s = ctx->stream;
+    size_t n = (size_t)nvec * st.dim;
+    ea::DArr<double> x(n, s), y(n, s);
+    EA_CK(cudaMemcpyAsync(x.p, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    if (prec == EAADC_FP64) ea::sigma_fp64(s, st, nvec, x.p, y.p);
+    else ea::sigma_mixed(s, st, nvec, x.p, y.p);
+    EA_CK(cudaMemcpyAsync(sigma_host, y.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    EA_CK(cudaStreamSynchronize(s));
+  });
+}
+
+eaadc_status eaadc_diagonal(eaadc_ctx* ctx, int state, double* diag_host) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    ea::State& st = get_state(ctx, state);
+    if (!diag_host) ea::fail(EAADC_ERR_ARG, "NULL output");
+    EA_CK(cudaMemcpyAsync(diag_host, st.diag.p, sizeof(double) * st.dim, cudaMemcpyDeviceToHost, ctx->stream));
+    EA_CK(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+eaadc_status eaadc_get_m11(eaadc_ctx* ctx, int state, double* m11_host) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    ea::State& st = get_state(ctx, state);
+    if (!m11_host) ea::fail(EAADC_ERR_ARG, "NULL output");
+    EA_CK(cudaMemcpyAsync(m11_host, st.M11.p, sizeof(double) * st.M11.n, cudaMemcpyDeviceToHost, ctx->stream));
+    EA_CK(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+eaadc_status eaadc_davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts* opts, double* omega,
+                            double* resnorm, int* iters) {
+  if (!ctx) return EAADC_ERR_ARG;
+  bool conv = true;
+  eaadc_status st = guarded(ctx, [&] {
+    set_device(ctx);
+    if (ctx->states.empty()) ea::fail(EAADC_ERR_STATE, "no states built");
+    if (nroots < 1 || !opts || !omega) ea::fail(EAADC_ERR_ARG, "bad arguments");
+    if (!(opts->tol > 0) || opts->maxit < 1) ea::fail(EAADC_ERR_ARG, "bad Davidson options");
+    ea::davidson(ctx, nroots, *opts, omega, resnorm, iters, &conv);
+  });
+  if (st == EAADC_OK && !conv) {
+    ctx->err = "Davidson did not converge within maxit";
+    return EAADC_ERR_NOCONV;
+  }
+  return st;
+}
+
+eaadc_status eaadc_get_eigvecs(eaadc_ctx* ctx, int state, double* vec_host) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    ea::State& st = get_state(ctx, state);
+    if (!vec_host) ea::fail(EAADC_ERR_ARG, "NULL output");
+    if (!st.nvecs) ea::fail(EAADC_ERR_STATE, "no eigenvectors (run eaadc_davidson first)");
+    EA_CK(cudaMemcpyAsync(vec_host, st.evecs.p, sizeof(double) * st.nvecs * st.dim, cudaMemcpyDeviceToHost,
+                          ctx->stream));
+    EA_CK(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+void eaadc_destroy(eaadc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = ctx->stream;
+  delete ctx;
+  cudaStreamSynchronize(s);
+}
+
+const char* eaadc_last_error(const eaadc_ctx* ctx) {
+  if (!ctx) return g_static_err.c_str();
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

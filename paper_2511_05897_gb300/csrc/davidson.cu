@@ -1,0 +1,351 @@
+// Block Davidson eigensolver on the device (Sec. II.A: M is diagonalised by
+// Davidson's method from sigma vectors).  All vector arithmetic is FP64 and
+// runs in this library's kernels; per iteration only the Ritz values, the
+// residual norms and the number of accepted new directions (a few doubles)
+// are read back to decide convergence.
+//
+// Readings (unstated in the paper): guesses are unit vectors on the nroots
+// lowest diagonal entries; the correction is r / (theta - D) with
+// |theta - D| floored at 1e-8; corrections are normalised, projected out of
+// the subspace twice (classical Gram-Schmidt) and then orthonormalised among
+// themselves by canonical orthogonalisation (eigenvectors of their Gram
+// matrix, directions with eigenvalue <= 1e-18 dropped); the subspace restarts
+// from the 2*nroots lowest Ritz vectors when it would exceed max_sub.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace ea {
+namespace {
+
+int gridn(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 16); }
+
+// partial min over a range, excluding listed indices
+__global__ void argmin_partial(const double* __restrict__ D, long long n, const int* __restrict__ excl, int nexcl,
+                               double* __restrict__ pv, long long* __restrict__ pi) {
+  double best = INFINITY;
+  long long bi = -1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    bool skip = false;
+    for (int e = 0; e < nexcl; ++e) skip |= (excl[e] == i);
+    if (skip) continue;
+    double d = D[i];
+    if (d < best || (d == best && i < bi)) { best = d; bi = i; }
+  }
+  __shared__ double sv[256];
+  __shared__ long long si[256];
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if (threadIdx.x < o) {
+      double v2 = sv[threadIdx.x + o];
+      long long i2 = si[threadIdx.x + o];
+      if (i2 >= 0 && (si[threadIdx.x] < 0 || v2 < sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x]))) {
+        sv[threadIdx.x] = v2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { pv[blockIdx.x] = sv[0]; pi[blockIdx.x] = si[0]; }
+}
+
+__global__ void argmin_final(const double* __restrict__ pv, const long long* __restrict__ pi, int np, int* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double best = INFINITY;
+  long long bi = -1;
+  for (int i = 0; i < np; ++i)
+    if (pi[i] >= 0 && (bi < 0 || pv[i] < best || (pv[i] == best && pi[i] < bi))) { best = pv[i]; bi = pi[i]; }
+  *out = (int)bi;
+}
+
+__global__ void set_units(double* __restrict__ V, long long n, const int* __restrict__ idx, int k) {
+  long long total = n * k;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(t / n);
+    long long i = t % n;
+    V[t] = (i == idx[r]) ? 1.0 : 0.0;
+  }
+}
+
+// C[z][i][j] partial dot products are reduced here: C = sum_z P[z]
+__global__ void reduce_partials(const double* __restrict__ P, int nz, int count, double* __restrict__ C, int ma,
+                                int mb, long long ldc) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nz; ++z) s += P[(long long)z * count + e];
+    C[(long long)(e / mb) * ldc + (e % mb)] = s;
+  }
+}
+
+__global__ void symmetrize(double* __restrict__ G, int m, long long ld, double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    int i = e / m, j = e % m;
+    out[e] = 0.5 * (G[i * ld + j] + G[j * ld + i]);
+  }
+}
+
+// R = SX - theta X, partial squared norms per (row, block)
+__global__ void residual_kernel(const double* __restrict__ SX, const double* __restrict__ X,
+                                const double* __restrict__ theta, double* __restrict__ R, long long n, int k,
+                                double* __restrict__ part) {
+  const int r = blockIdx.y;
+  const double th = theta[r];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = SX[r * n + i] - th * X[r * n + i];
+    R[r * n + i] = v;
+    acc += v * v;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[r * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void rownorm_partial(const double* __restrict__ X, long long n, double* __restrict__ part) {
+  const int r = blockIdx.y;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = X[r * n + i];
+    acc += v * v;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[r * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void finish_norms(const double* __restrict__ part, int nb, int k, double* __restrict__ out) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[r * nb + b];
+  out[r] = sqrt(s);
+}
+
+// rows of X scaled by 1/norm (norm > 0)
+__global__ void scale_rows(double* __restrict__ X, long long n, const double* __restrict__ nrm) {
+  const int r = blockIdx.y;
+  double sc = nrm[r] > 0 ? 1.0 / nrm[r] : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    X[r * n + i] *= sc;
+}
+
+// Dn[j] = R[rows[j]] / (theta[rows[j]] - D), |theta - D| floored at 1e-8
+__global__ void precond_kernel(const double* __restrict__ R, const double* __restrict__ theta,
+                               const double* __restrict__ D, const int* __restrict__ rows, int nn, long long n,
+                               double* __restrict__ Dn) {
+  const int j = blockIdx.y;
+  const int r = rows[j];
+  const double th = theta[r];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double den = th - D[i];
+    if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+    Dn[j * n + i] = R[r * n + i] / den;
+  }
+}
+
+// canonical orthogonalisation coefficients: coef[j][c] = Z[j][src(c)] / sqrt(lam[src(c)])
+// for eigenvalues above thr, largest first; count written to *cnt.
+__global__ void canon_coef(const double* __restrict__ Z, const double* __restrict__ lam, int nn, double thr,
+                           double* __restrict__ coef, int* __restrict__ cnt) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int c = 0;
+  for (int e = nn - 1; e >= 0; --e) {
+    if (lam[e] > thr) {
+      double sc = 1.0 / sqrt(lam[e]);
+      for (int j = 0; j < nn; ++j) coef[j * nn + c] = Z[j * nn + e] * sc;
+      ++c;
+    }
+  }
+  *cnt = c;
+}
+
+}  // namespace
+
+// C[i][j] = sum_t A[i][t] B[j][t] for i < ma, j < mb (split over t)
+static void gram(cudaStream_t s, const double* A, int ma, const double* B, int mb, long long n, double* C,
+                 long long ldc) {
+  if (ma <= 0 || mb <= 0) return;
+  int nz = (int)std::min<long long>(std::max<long long>(1, n / 4096), 256);
+  long long chunk = (n + nz - 1) / nz;
+  nz = (int)((n + chunk - 1) / chunk);
+  DArr<double> P((size_t)nz * ma * mb, s);
+  fill(s, P.p, P.n, 0.0);
+  // full chunks through the batched GEMM, the tail separately
+  int nfull = (int)(n / chunk);
+  if (nfull > 0) {
+    GemmBatch bt;
+    bt.nb1 = nfull;
+    bt.sA1 = chunk;
+    bt.sB1 = chunk;
+    bt.sC1 = (long long)ma * mb;
+    dgemm(s, false, true, ma, mb, (int)chunk, 1.0, A, n, B, n, 0.0, P.p, mb, bt);
+  }
+  long long tail = n - (long long)nfull * chunk;
+  if (tail > 0)
+    dgemm(s, false, true, ma, mb, (int)tail, 1.0, A + nfull * chunk, n, B + nfull * chunk, n, 0.0,
+          P.p + (long long)nfull * ma * mb, mb);
+  int count = ma * mb;
+  reduce_partials<<<(count + 255) / 256, 256, 0, s>>>(P.p, nz, count, C, ma, mb, ldc);
+  EA_LAUNCH();
+}
+
+static void row_norms(cudaStream_t s, const double* X, int k, long long n, double* out) {
+  int nb = std::min(256, (int)std::max<long long>(1, (n + 255) / 256));
+  DArr<double> part((size_t)k * nb, s);
+  rownorm_partial<<<dim3(nb, k), 256, 0, s>>>(X, n, part.p);
+  EA_LAUNCH();
+  finish_norms<<<1, 64, 0, s>>>(part.p, nb, k, out);
+  EA_LAUNCH();
+}
+
+static void apply_sigma(cudaStream_t s, State& st, int prec, int nvec, const double* x, double* y) {
+  if (prec == EAADC_FP64) sigma_fp64(s, st, nvec, x, y);
+  else sigma_mixed(s, st, nvec, x, y);
+}
+
+// One Davidson phase at precision `prec` starting from `k0` orthonormal rows in V.
+// Returns true if converged.
+static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaadc_davidson_opts& opt, DArr<double>& V,
+                           DArr<double>& S, int mmax, int k0, std::vector<double>& theta, std::vector<double>& rn,
+                           int& iters, DArr<double>& Xr) {
+  const long long n = st.dim;
+  int m = k0;
+  apply_sigma(s, st, prec, m, V.p, S.p);
+  DArr<double> G((size_t)mmax * mmax, s), Gs((size_t)mmax * mmax, s), w((size_t)mmax, s), U((size_t)mmax * mmax, s);
+  DArr<double> SX((size_t)k * n, s), R((size_t)k * n, s), Dn((size_t)k * n, s), Dtmp((size_t)k * n, s);
+  DArr<double> rnd((size_t)k, s), C((size_t)mmax * k, s), Gd((size_t)k * k, s), Zd((size_t)k * k, s),
+      ld((size_t)k, s), coef((size_t)k * k, s), nrm((size_t)k, s);
+  DArr<int> rows((size_t)k, s), cnt(1, s);
+  int nb = std::min(256, (int)std::max<long long>(1, (n + 255) / 256));
+  DArr<double> part((size_t)k * nb, s);
+  std::vector<double> th_old(k, INFINITY);
+  theta.assign(k, 0.0);
+  rn.assign(k, 0.0);
+  bool conv = false;
+  for (int it = 1; it <= opt.maxit; ++it) {
+    iters++;
+    gram(s, V.p, m, S.p, m, n, G.p, m);
+    symmetrize<<<(m * m + 255) / 256, 256, 0, s>>>(G.p, m, m, Gs.p);
+    EA_LAUNCH();
+    jacobi_eigh(s, m, Gs.p, w.p, U.p);
+    // Ritz vectors and their sigma: X = U[:, :k]^T V
+    dgemm(s, true, false, k, (int)n, m, 1.0, U.p, m, V.p, n, 0.0, Xr.p, n);
+    dgemm(s, true, false, k, (int)n, m, 1.0, U.p, m, S.p, n, 0.0, SX.p, n);
+    residual_kernel<<<dim3(nb, k), 256, 0, s>>>(SX.p, Xr.p, w.p, R.p, n, k, part.p);
+    EA_LAUNCH();
+    finish_norms<<<1, 64, 0, s>>>(part.p, nb, k, rnd.p);
+    EA_LAUNCH();
+    EA_CK(cudaMemcpyAsync(theta.data(), w.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    EA_CK(cudaMemcpyAsync(rn.data(), rnd.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    EA_CK(cudaStreamSynchronize(s));
+    for (int r = 0; r < k; ++r)
+      if (!std::isfinite(theta[r]) || !std::isfinite(rn[r])) fail(EAADC_ERR_NONFINITE, "davidson: non-finite Ritz value or residual");
+    bool all = true;
+    std::vector<int> un;
+    for (int r = 0; r < k; ++r) {
+      bool c = rn[r] <= opt.tol && std::fabs(theta[r] - th_old[r]) <= opt.etol;
+      all &= c;
+      if (rn[r] > opt.tol) un.push_back(r);
+    }
+    th_old = theta;
+    if (all) { conv = true; break; }
+    if (un.empty()) continue;  // residuals small, Ritz values still moving: iterate on same space
+    int nn = (int)un.size();
+    EA_CK(cudaMemcpyAsync(rows.p, un.data(), sizeof(int) * nn, cudaMemcpyHostToDevice, s));
+    precond_kernel<<<dim3(nb, nn), 256, 0, s>>>(R.p, w.p, st.diag.p, rows.p, nn, n, Dn.p);
+    EA_LAUNCH();
+    row_norms(s, Dn.p, nn, n, nrm.p);
+    scale_rows<<<dim3(nb, nn), 256, 0, s>>>(Dn.p, n, nrm.p);
+    EA_LAUNCH();
+    for (int pass = 0; pass < 2; ++pass) {
+      gram(s, V.p, m, Dn.p, nn, n, C.p, nn);
+      dgemm(s, true, false, nn, (int)n, m, -1.0, C.p, nn, V.p, n, 1.0, Dn.p, n);
+    }
+    gram(s, Dn.p, nn, Dn.p, nn, n, Gd.p, nn);
+    symmetrize<<<1, 256, 0, s>>>(Gd.p, nn, nn, Zd.p);
+    EA_LAUNCH();
+    DArr<double> Zv((size_t)nn * nn, s);
+    jacobi_eigh(s, nn, Zd.p, ld.p, Zv.p);
+    canon_coef<<<1, 1, 0, s>>>(Zv.p, ld.p, nn, 1e-18, coef.p, cnt.p);
+    EA_LAUNCH();
+    int nacc = 0;
+    EA_CK(cudaMemcpyAsync(&nacc, cnt.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    EA_CK(cudaStreamSynchronize(s));
+    if (nacc == 0) break;
+    if (m + nacc > mmax) {
+      int keep = std::min(std::max(2 * k, k), m);
+      keep = std::min(keep, mmax - nacc);
+      DArr<double> T((size_t)keep * n, s);
+      dgemm(s, true, false, keep, (int)n, m, 1.0, U.p, m, V.p, n, 0.0, T.p, n);
+      EA_CK(cudaMemcpyAsync(V.p, T.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, s));
+      dgemm(s, true, false, keep, (int)n, m, 1.0, U.p, m, S.p, n, 0.0, T.p, n);
+      EA_CK(cudaMemcpyAsync(S.p, T.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, s));
+      m = keep;
+    }
+    // new orthonormal directions: coef^T Dn
+    dgemm(s, true, false, nacc, (int)n, nn, 1.0, coef.p, nn, Dn.p, n, 0.0, V.p + (long long)m * n, n);
+    apply_sigma(s, st, prec, nacc, V.p + (long long)m * n, S.p + (long long)m * n);
+    m += nacc;
+  }
+  return conv;
+}
+
+void davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts& opt, double* omega, double* resnorm, int* iters,
+              bool* converged) {
+  cudaStream_t s = ctx->stream;
+  *converged = true;
+  for (size_t si = 0; si < ctx->states.size(); ++si) {
+    State& st = *ctx->states[si];
+    const long long n = st.dim;
+    int k = (int)std::min<long long>(nroots, n);
+    int mmax = (int)std::min<long long>(std::min(opt.max_sub, 96), n);
+    if (mmax < 2 * k) mmax = (int)std::min<long long>(2 * k, n);
+    if (mmax > 96) fail(EAADC_ERR_ARG, "davidson: subspace would exceed 96 vectors");
+    DArr<double> V((size_t)mmax * n, s), S((size_t)mmax * n, s);
+    st.evecs.alloc((size_t)k * n, s);
+    st.nvecs = k;
+    // guesses on the k lowest diagonal entries
+    DArr<int> idx((size_t)k, s);
+    int npart = std::min(256, (int)std::max<long long>(1, (n + 255) / 256));
+    DArr<double> pv((size_t)npart, s);
+    DArr<long long> pi((size_t)npart, s);
+    for (int r = 0; r < k; ++r) {
+      argmin_partial<<<npart, 256, 0, s>>>(st.diag.p, n, idx.p, r, pv.p, pi.p);
+      EA_LAUNCH();
+      argmin_final<<<1, 1, 0, s>>>(pv.p, pi.p, npart, idx.p + r);
+      EA_LAUNCH();
+    }
+    set_units<<<gridn(n * k), 256, 0, s>>>(V.p, n, idx.p, k);
+    EA_LAUNCH();
+    std::vector<double> theta, rn;
+    int it = 0;
+    bool conv = davidson_phase(s, st, k, opt.prec, opt, V, S, mmax, k, theta, rn, it, st.evecs);
+    if (opt.prec != EAADC_FP64 && opt.refine) {
+      // FP64 refinement from the mixed-precision Ritz vectors
+      EA_CK(cudaMemcpyAsync(V.p, st.evecs.p, sizeof(double) * k * n, cudaMemcpyDeviceToDevice, s));
+      conv = davidson_phase(s, st, k, EAADC_FP64, opt, V, S, mmax, k, theta, rn, it, st.evecs);
+    }
+    for (int r = 0; r < k; ++r) {
+      omega[si * nroots + r] = theta[r];
+      if (resnorm) resnorm[si * nroots + r] = rn[r];
+    }
+    if (iters) iters[si] = it;
+    *converged &= conv;
+  }
+}
+
+}  // namespace ea

@@ -1,0 +1,146 @@
+// Internal declarations of the EA-ADC library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <initializer_list>
+#include "eaadc.h"
+
+namespace ea {
+
+struct Error {
+  eaadc_status st;
+  std::string msg;
+};
+
+[[noreturn]] void fail(eaadc_status st, const std::string& msg);
+
+#define EA_CK(x)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (x);                                                                \
+    if (e_ != cudaSuccess)                                                               \
+      ::ea::fail(EAADC_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_) +       \
+                                     " at " + __FILE__ + ":" + std::to_string(__LINE__)); \
+  } while (0)
+
+#define EA_LAUNCH() EA_CK(cudaGetLastError())
+
+// ------------------------------------------------------------ device memory
+// Stream-ordered device array owned by its creator.
+template <class T>
+struct DArr {
+  T* p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = nullptr;
+  DArr() = default;
+  DArr(size_t n_, cudaStream_t s_) { alloc(n_, s_); }
+  void alloc(size_t n_, cudaStream_t s_) {
+    release();
+    n = n_;
+    s = s_;
+    if (n) {
+      cudaError_t e = cudaMallocAsync((void**)&p, n * sizeof(T), s);
+      if (e != cudaSuccess) {
+        p = nullptr;
+        n = 0;
+        cudaGetLastError();
+        fail(EAADC_ERR_ALLOC, "device allocation of " + std::to_string(n_ * sizeof(T)) + " bytes failed");
+      }
+    }
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    n = 0;
+  }
+  ~DArr() { release(); }
+  DArr(const DArr&) = delete;
+  DArr& operator=(const DArr&) = delete;
+  DArr(DArr&& o) noexcept : p(o.p), n(o.n), s(o.s) { o.p = nullptr; o.n = 0; }
+  DArr& operator=(DArr&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; s = o.s; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+};
+
+using bf16 = __nv_bfloat16;
+
+// ------------------------------------------------------------- FP64 toolkit
+// Row-major GEMM: C = alpha * op(A) * op(B) + beta * C, op(X) = X or X^T.
+// A is M x K (or K x M if ta) with row stride lda; B is K x N (or N x K if tb).
+// Two-level batch: batch index z = z1 * nb2 + z2 adds z1*s?1 + z2*s?2.
+struct GemmBatch {
+  int nb1 = 1, nb2 = 1;
+  long long sA1 = 0, sA2 = 0, sB1 = 0, sB2 = 0, sC1 = 0, sC2 = 0;
+};
+void dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
+           long long lda, const double* B, long long ldb, double beta, double* C, long long ldc,
+           const GemmBatch& bt = GemmBatch());
+
+// dst = alpha * permute(src) + beta * dst; src has dims sdims, dst axis i is src axis perm[i].
+void permute(cudaStream_t s, const double* src, const std::vector<int>& sdims,
+             const std::vector<int>& perm, double* dst, double alpha = 1.0, double beta = 0.0);
+
+// out[.., b, c] = alpha * (c1 * in[.., b, c] + c2 * in[.., c, b]) + beta * out[.., b, c]
+// for `nmat` consecutive v x v matrices with strides (in_stride, out_stride).
+void pair_combine(cudaStream_t s, const double* in, long long in_stride, double* out,
+                  long long out_stride, int nmat, int v, double c1, double c2, double alpha, double beta);
+
+// Generic helpers.
+void fill(cudaStream_t s, double* p, size_t n, double val);
+void axpby(cudaStream_t s, size_t n, double a, const double* x, double b, double* y);  // y = a x + b y
+
+// Two-operand tensor contraction (einsum without batch labels), FP64.
+struct Tens {
+  double* p;
+  std::vector<int> dims;
+  size_t size() const { size_t n = 1; for (int d : dims) n *= (size_t)d; return n; }
+};
+void einsum(cudaStream_t s, const char* spec, double alpha, const Tens& A, const Tens& B, double beta,
+            const Tens& C);
+
+// ------------------------------------------------------------- problem data
+struct State {
+  int o = 0, v = 0, naux = 0;
+  long long dim = 0;
+  int order = 3;
+  double x3 = 1.0;
+  DArr<double> eo, ev;            // [o], [v]
+  DArr<double> Boo, Bov, Bvv;     // [naux][o][o], [naux][o][v], [naux][v][v]
+  DArr<double> tau;               // [o][o][v][v]  (ia|jb)/D
+  DArr<double> Kmat, Jmat;        // [(k,b)][(l,d)] = (bd|lk) ; [(k,c)][(l,d)] = (ck|ld)
+  DArr<double> M11;               // [v][v]
+  DArr<double> diag;              // [dim] Davidson diagonal
+  // mixed-precision operands (built lazily)
+  DArr<bf16> Bvv_bf, Kmat_bf, Jmat_bf;
+  bool mixed_ready = false;
+  // last Davidson solution
+  DArr<double> evecs;             // [nroots][dim]
+  int nvecs = 0;
+};
+
+}  // namespace ea
+
+struct eaadc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int o = 0, v = 0, naux = 0;
+  ea::DArr<double> eo, ev, Boo, Bov, Bvv;
+  std::vector<ea::State*> states;
+  std::string err;
+  ~eaadc_ctx();
+};
+
+namespace ea {
+void build_state_intermediates(eaadc_ctx* ctx, State& st);
+void sigma_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y);
+void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y);
+void make_diagonal(cudaStream_t s, State& st);
+void davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts& opt, double* omega,
+              double* resnorm, int* iters, bool* converged);
+// Dense symmetric eigensolver (cyclic Jacobi, one CTA): A [m][m] (destroyed),
+// eigenvalues ascending into w[m], eigenvectors as columns of U [m][m].
+void jacobi_eigh(cudaStream_t s, int m, double* A, double* w, double* U);
+}  // namespace ea

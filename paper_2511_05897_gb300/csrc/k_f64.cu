@@ -1,0 +1,410 @@
+// FP64 building blocks: batched DGEMM, tensor permutation, pair combinations,
+// a two-operand contraction engine and a one-CTA Jacobi eigensolver.
+#include "internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+
+namespace ea {
+
+[[noreturn]] void fail(eaadc_status st, const std::string& msg) { throw Error{st, msg}; }
+
+// ------------------------------------------------------------------- DGEMM
+namespace {
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <bool TA, bool TB, bool BETA0>
+__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha,
+                                                    const double* __restrict__ A, long long lda,
+                                                    const double* __restrict__ B, long long ldb,
+                                                    double beta, double* __restrict__ C, long long ldc,
+                                                    GemmBatch bt) {
+  const int z = blockIdx.z;
+  const int z1 = z / bt.nb2, z2 = z % bt.nb2;
+  A += z1 * bt.sA1 + z2 * bt.sA2;
+  B += z1 * bt.sB1 + z2 * bt.sB2;
+  C += z1 * bt.sC1 + z2 * bt.sC2;
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int i = tid + 256 * r;
+      int mm, kk;
+      if (TA) { mm = i % BM; kk = i / BM; } else { kk = i % BK; mm = i / BK; }
+      int gm = m0 + mm, gk = k0 + kk;
+      double a = 0.0;
+      if (gm < M && gk < K) a = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+      As[kk][mm] = a;
+      int nn;
+      if (TB) { kk = i % BK; nn = i / BK; } else { nn = i % BN; kk = i / BN; }
+      int gn = n0 + nn;
+      gk = k0 + kk;
+      double b = 0.0;
+      if (gn < N && gk < K) b = TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
+      Bs[kk][nn] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      double* c = C + (long long)gm * ldc + gn;
+      *c = BETA0 ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
+    }
+  }
+}
+
+template <bool TA, bool TB>
+void dgemm_t(cudaStream_t s, int M, int N, int K, double alpha, const double* A, long long lda,
+             const double* B, long long ldb, double beta, double* C, long long ldc, const GemmBatch& bt) {
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, bt.nb1 * bt.nb2);
+  if (beta == 0.0)
+    dgemm_kernel<TA, TB, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  else
+    dgemm_kernel<TA, TB, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  EA_LAUNCH();
+}
+}  // namespace
+
+void dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
+           long long lda, const double* B, long long ldb, double beta, double* C, long long ldc,
+           const GemmBatch& bt) {
+  if (M <= 0 || N <= 0 || bt.nb1 * bt.nb2 <= 0) return;
+  if (bt.nb1 * bt.nb2 > 65535) fail(EAADC_ERR_ARG, "dgemm: batch too large");
+  if ((M + BM - 1) / BM > 65535) fail(EAADC_ERR_ARG, "dgemm: M too large");
+  if (ta && tb) dgemm_t<true, true>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  else if (ta) dgemm_t<true, false>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  else if (tb) dgemm_t<false, true>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  else dgemm_t<false, false>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+}
+
+// ----------------------------------------------------------------- permute
+namespace {
+struct PermArgs {
+  int nd;
+  long long ddim[8];
+  long long sstride[8];  // stride in src of dst axis i
+};
+
+__global__ void permute_kernel(const double* __restrict__ src, double* __restrict__ dst, long long total,
+                               PermArgs pa, double alpha, double beta) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long r = idx, off = 0;
+    for (int i = pa.nd - 1; i >= 0; --i) {
+      long long c = r % pa.ddim[i];
+      r /= pa.ddim[i];
+      off += c * pa.sstride[i];
+    }
+    double val = alpha * src[off];
+    dst[idx] = (beta == 0.0) ? val : val + beta * dst[idx];
+  }
+}
+
+int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
+}  // namespace
+
+void permute(cudaStream_t s, const double* src, const std::vector<int>& sdims, const std::vector<int>& perm,
+             double* dst, double alpha, double beta) {
+  int nd = (int)sdims.size();
+  if (nd > 8 || (int)perm.size() != nd) fail(EAADC_ERR_ARG, "permute: bad rank");
+  long long st[8];
+  long long acc = 1;
+  for (int i = nd - 1; i >= 0; --i) { st[i] = acc; acc *= sdims[i]; }
+  PermArgs pa;
+  pa.nd = nd;
+  for (int i = 0; i < nd; ++i) { pa.ddim[i] = sdims[perm[i]]; pa.sstride[i] = st[perm[i]]; }
+  if (acc == 0) return;
+  permute_kernel<<<grid_for(acc), 256, 0, s>>>(src, dst, acc, pa, alpha, beta);
+  EA_LAUNCH();
+}
+
+// ------------------------------------------------------------ pair combine
+namespace {
+__global__ void pair_combine_kernel(const double* __restrict__ in, long long in_stride, double* __restrict__ out,
+                                    long long out_stride, int nmat, int v, double c1, double c2, double alpha,
+                                    double beta) {
+  // 32x32 tiles of one matrix; transposed partner read through shared memory
+  __shared__ double tileT[32][33];
+  const int m = blockIdx.z;
+  const int b0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const double* I = in + (long long)m * in_stride;
+  double* O = out + (long long)m * out_stride;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  // load in[c0+.., b0+..] so that tileT[tx][ty] holds in[c][b] with c = c0+ty, b = b0+tx
+  for (int r = ty; r < 32; r += 8) {
+    int c = c0 + r, b = b0 + tx;
+    tileT[tx][r] = (c < v && b < v) ? I[(long long)c * v + b] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    int b = b0 + r, c = c0 + tx;
+    if (b < v && c < v) {
+      double val = alpha * (c1 * I[(long long)b * v + c] + c2 * tileT[r][tx]);
+      double* o = O + (long long)b * v + c;
+      *o = (beta == 0.0) ? val : val + beta * (*o);
+    }
+  }
+}
+
+__global__ void fill_kernel(double* p, long long n, double val) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = val;
+}
+__global__ void axpby_kernel(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+}  // namespace
+
+void pair_combine(cudaStream_t s, const double* in, long long in_stride, double* out, long long out_stride,
+                  int nmat, int v, double c1, double c2, double alpha, double beta) {
+  if (nmat <= 0 || v <= 0) return;
+  if (nmat > 65535) fail(EAADC_ERR_ARG, "pair_combine: too many matrices");
+  dim3 grid((v + 31) / 32, (v + 31) / 32, nmat);
+  pair_combine_kernel<<<grid, dim3(32, 8), 0, s>>>(in, in_stride, out, out_stride, nmat, v, c1, c2, alpha, beta);
+  EA_LAUNCH();
+}
+
+void fill(cudaStream_t s, double* p, size_t n, double val) {
+  if (!n) return;
+  fill_kernel<<<grid_for((long long)n), 256, 0, s>>>(p, (long long)n, val);
+  EA_LAUNCH();
+}
+void axpby(cudaStream_t s, size_t n, double a, const double* x, double b, double* y) {
+  if (!n) return;
+  axpby_kernel<<<grid_for((long long)n), 256, 0, s>>>((long long)n, a, x, b, y);
+  EA_LAUNCH();
+}
+
+// ------------------------------------------------------------------ einsum
+void einsum(cudaStream_t s, const char* spec, double alpha, const Tens& A, const Tens& B, double beta,
+            const Tens& C) {
+  std::string sp(spec);
+  size_t comma = sp.find(','), arrow = sp.find("->");
+  if (comma == std::string::npos || arrow == std::string::npos) fail(EAADC_ERR_ARG, "einsum: bad spec");
+  std::string la = sp.substr(0, comma), lb = sp.substr(comma + 1, arrow - comma - 1), lc = sp.substr(arrow + 2);
+  if (la.size() != A.dims.size() || lb.size() != B.dims.size() || lc.size() != C.dims.size())
+    fail(EAADC_ERR_ARG, std::string("einsum: rank mismatch in ") + spec);
+  std::map<char, int> dim;
+  auto reg = [&](const std::string& l, const std::vector<int>& d) {
+    for (size_t i = 0; i < l.size(); ++i) {
+      auto it = dim.find(l[i]);
+      if (it != dim.end() && it->second != d[i]) fail(EAADC_ERR_ARG, std::string("einsum: dim mismatch in ") + spec);
+      dim[l[i]] = d[i];
+    }
+  };
+  reg(la, A.dims); reg(lb, B.dims); reg(lc, C.dims);
+  std::string fa, fb, kc;
+  for (char c : la) {
+    bool inb = lb.find(c) != std::string::npos, inc = lc.find(c) != std::string::npos;
+    if (inb && inc) fail(EAADC_ERR_ARG, std::string("einsum: batch label unsupported in ") + spec);
+    if (!inb && !inc) fail(EAADC_ERR_ARG, std::string("einsum: summed-out label unsupported in ") + spec);
+    if (inc) fa += c; else kc += c;
+  }
+  for (char c : lb) {
+    bool ina = la.find(c) != std::string::npos, inc = lc.find(c) != std::string::npos;
+    if (!ina && !inc) fail(EAADC_ERR_ARG, std::string("einsum: summed-out label unsupported in ") + spec);
+    if (inc) fb += c;
+  }
+  auto prod = [&](const std::string& l) { long long p = 1; for (char c : l) p *= dim[c]; return p; };
+  long long M = prod(fa), N = prod(fb), K = prod(kc);
+  auto perm_of = [&](const std::string& from, const std::string& to) {
+    std::vector<int> p;
+    for (char c : to) p.push_back((int)from.find(c));
+    return p;
+  };
+  auto is_id = [](const std::vector<int>& p) { for (size_t i = 0; i < p.size(); ++i) if (p[i] != (int)i) return false; return true; };
+  // Operand A is used as stored when its labels read [fa kc] (plain) or
+  // [kc fa] (transposed); B likewise with [fb kc] or [kc fb].  Otherwise it is
+  // permuted to [free..., contracted...].
+  DArr<double> ta, tb, tc;
+  const double* pa = A.p;
+  bool transA = false;
+  long long ldA = K;
+  if (la == fa + kc) {
+  } else if (la == kc + fa) {
+    transA = true;
+    ldA = M;
+  } else {
+    ta.alloc(A.size(), s);
+    permute(s, A.p, A.dims, perm_of(la, fa + kc), ta.p);
+    pa = ta.p;
+  }
+  const double* pb = B.p;
+  bool transB = true;  // B used as N x K
+  long long ldB = K;
+  if (lb == fb + kc) {
+  } else if (lb == kc + fb) {
+    transB = false;
+    ldB = N;
+  } else {
+    tb.alloc(B.size(), s);
+    permute(s, B.p, B.dims, perm_of(lb, fb + kc), tb.p);
+    pb = tb.p;
+  }
+  std::string lt = fa + fb;
+  std::vector<int> pC = perm_of(lt, lc);
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) fail(EAADC_ERR_ARG, "einsum: extent too large");
+  if (is_id(pC)) {
+    dgemm(s, transA, transB, (int)M, (int)N, (int)K, alpha, pa, ldA, pb, ldB, beta, C.p, N);
+  } else {
+    tc.alloc((size_t)(M * N), s);
+    dgemm(s, transA, transB, (int)M, (int)N, (int)K, 1.0, pa, ldA, pb, ldB, 0.0, tc.p, N);
+    std::vector<int> tdims;
+    for (char c : lt) tdims.push_back(dim[c]);
+    permute(s, tc.p, tdims, pC, C.p, alpha, beta);
+  }
+}
+
+// ------------------------------------------------------------------ Jacobi
+namespace {
+__global__ void __launch_bounds__(1024) jacobi_kernel(int m, double* __restrict__ Ag, double* __restrict__ w,
+                                                      double* __restrict__ Ug, int max_sweeps) {
+  extern __shared__ double sm[];
+  const int n = (m + 1) & ~1;  // even number of players (dummy index m if m is odd)
+  double* A = sm;              // [m][m]
+  double* U = sm + (size_t)m * m;
+  double* cs = U + (size_t)m * m;  // [n/2] cos
+  double* sn = cs + n / 2;         // [n/2] sin
+  int* pp = (int*)(sn + n / 2);    // [n/2]
+  int* qq = pp + n / 2;
+  __shared__ double red[32];
+  __shared__ int stop;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < m * m; i += nt) {
+    A[i] = Ag[i];
+    U[i] = (i / m == i % m) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence: off-diagonal vs diagonal magnitude
+    double off = 0.0, dg = 0.0;
+    for (int i = tid; i < m * m; i += nt) {
+      double a = A[i];
+      if (i / m == i % m) dg += a * a; else off += a * a;
+    }
+    for (int o = 16; o; o >>= 1) { off += __shfl_xor_sync(0xffffffffu, off, o); dg += __shfl_xor_sync(0xffffffffu, dg, o); }
+    if ((tid & 31) == 0) red[tid >> 5] = off;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int i = 0; i < (nt + 31) / 32; ++i) t += red[i];
+      red[0] = t;
+    }
+    __syncthreads();
+    off = red[0];
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = dg;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int i = 0; i < (nt + 31) / 32; ++i) t += red[i];
+      stop = (off <= 1e-30 * t) || (off < 1e-300);
+    }
+    __syncthreads();
+    if (stop) break;
+    for (int step = 0; step < n - 1; ++step) {
+      for (int i = tid; i < n / 2; i += nt) {
+        int a = (i == 0) ? 0 : 1 + (i - 1 + step) % (n - 1);
+        int j = n - 1 - i;
+        int b = 1 + (j - 1 + step) % (n - 1);
+        int p = min(a, b), q = max(a, b);
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          double apq = A[p * m + q];
+          if (fabs(apq) > 1e-300) {
+            double th = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+            double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        pp[i] = p; qq[i] = q; cs[i] = c; sn[i] = s;
+      }
+      __syncthreads();
+      // A <- A J (columns p, q) and U <- U J
+      for (int e = tid; e < (n / 2) * m; e += nt) {
+        int i = e / m, r = e % m;
+        int p = pp[i], q = qq[i];
+        if (q >= m) continue;
+        double c = cs[i], s = sn[i];
+        double ap = A[r * m + p], aq = A[r * m + q];
+        A[r * m + p] = c * ap - s * aq;
+        A[r * m + q] = s * ap + c * aq;
+        double up = U[r * m + p], uq = U[r * m + q];
+        U[r * m + p] = c * up - s * uq;
+        U[r * m + q] = s * up + c * uq;
+      }
+      __syncthreads();
+      // A <- J^T A (rows p, q)
+      for (int e = tid; e < (n / 2) * m; e += nt) {
+        int i = e / m, r = e % m;
+        int p = pp[i], q = qq[i];
+        if (q >= m) continue;
+        double c = cs[i], s = sn[i];
+        double ap = A[p * m + r], aq = A[q * m + r];
+        A[p * m + r] = c * ap - s * aq;
+        A[q * m + r] = s * ap + c * aq;
+      }
+      __syncthreads();
+    }
+  }
+  // sort eigenvalues ascending (selection by rank; ties broken by index)
+  for (int i = tid; i < m; i += nt) {
+    double di = A[i * m + i];
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      double dj = A[j * m + j];
+      rank += (dj < di) || (dj == di && j < i);
+    }
+    w[rank] = di;
+    for (int r = 0; r < m; ++r) Ug[r * m + rank] = U[r * m + i];
+  }
+}
+}  // namespace
+
+void jacobi_eigh(cudaStream_t s, int m, double* A, double* w, double* U) {
+  if (m <= 0) return;
+  if (m > 96) fail(EAADC_ERR_ARG, "jacobi_eigh: m > 96");
+  int n = (m + 1) & ~1;
+  size_t smem = sizeof(double) * (2 * (size_t)m * m + n) + sizeof(int) * n;
+  static bool attr = false;
+  if (!attr) {
+    EA_CK(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    attr = true;
+  }
+  jacobi_kernel<<<1, 1024, smem, s>>>(m, A, w, U, 60);
+  EA_LAUNCH();
+}
+
+}  // namespace ea

@@ -1,0 +1,124 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs.  FP64 mode: elementwise to ~1e-12 relative for sigma and
+the 1p/1p block, eigenvalues to 1e-8 Eh."""
+import os
+
+import numpy as np
+import pytest
+
+from synth import config_problem, make_problem
+from oracle import restricted as R
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def E():
+    import __graft_entry__ as g
+
+    g.build()
+    import paper_2511_05897_gb300 as mod
+
+    return mod
+
+
+def _ctx(E, pr, order=3, x3=1.0):
+    ctx = E.eaadc_init(pr["o"], pr["v"], pr["naux"], pr["eps_occ"], pr["eps_vir"], pr["B"], 0)
+    E.eaadc_build_canonical(ctx, order, x3)
+    return ctx
+
+
+# sizes: degenerate, ragged, several 64-wide GEMM tiles with a tail
+CASES = [(1, 1, 1, 1.0, 2), (1, 2, 3, 2.0, 4), (2, 3, 5, 3.0, 6), (3, 9, 24, 6.0, 5), (4, 13, 40, 8.0, 9),
+         (2, 70, 30, 10.0, 3), (5, 20, 60, 15.0, 1)]
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("o,v,naux,decay,seed", CASES)
+def test_m11_and_sigma_match_oracle(E, o, v, naux, decay, seed, order):
+    pr = make_problem(o, v, naux, decay, seed)
+    p = R.Problem(pr["eps_occ"], pr["eps_vir"], pr["B"])
+    sig = R.Sigma(p, order)
+    ctx = _ctx(E, pr, order)
+    try:
+        m11 = E.eaadc_get_m11(ctx, 0)
+        assert np.abs(m11 - sig.M11).max() <= 1e-12 * np.abs(sig.M11).max()
+        vp, npx, dim = E.eaadc_state_info(ctx, 0)
+        assert (vp, npx, dim) == (v, naux, v + o * v * v)
+        x = np.random.default_rng(seed).standard_normal((3, dim))
+        ref = sig(x)
+        got = E.eaadc_sigma_host(ctx, 0, x)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+        d = E.eaadc_diagonal(ctx, 0)
+        assert np.abs(d - sig.diagonal()).max() <= 1e-14 * np.abs(d).max()
+    finally:
+        E.eaadc_destroy(ctx)
+
+
+def test_sigma_device_pointers_and_x3(E):
+    """eaadc_sigma on caller-owned device buffers; x3 scales only M^(3)."""
+    import torch
+
+    pr = make_problem(3, 9, 24, 6.0, 11)
+    p = R.Problem(pr["eps_occ"], pr["eps_vir"], pr["B"])
+    ctx = _ctx(E, pr, 3, 0.5)
+    try:
+        M = R.explicit_matrix(p, 3, 0.5)
+        x = torch.randn(2, M.shape[0], dtype=torch.float64, device="cuda:0")
+        y = torch.empty_like(x)
+        E.eaadc_sigma(ctx, 0, 2, x.data_ptr(), y.data_ptr(), E.EAADC_FP64,
+                      torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        ref = x.cpu().numpy() @ M
+        assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    finally:
+        E.eaadc_destroy(ctx)
+
+
+def test_davidson_tiny_equals_dense(E):
+    pr = config_problem("tiny")
+    p = R.Problem(pr["eps_occ"], pr["eps_vir"], pr["B"])
+    ref = np.linalg.eigvalsh(R.explicit_matrix(p, 3))[:4]
+    ctx = _ctx(E, pr)
+    try:
+        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-8)
+        assert st == 0
+        assert np.abs(om[0] - ref).max() <= 1e-8
+        vecs = E.eaadc_get_eigvecs(ctx, 0, 4)
+        assert np.abs(vecs @ vecs.T - np.eye(4)).max() < 1e-10
+    finally:
+        E.eaadc_destroy(ctx)
+
+
+def test_davidson_edge_one_virtual(E):
+    pr = make_problem(1, 1, 1, 1.0, 2)
+    p = R.Problem(pr["eps_occ"], pr["eps_vir"], pr["B"])
+    ref = np.linalg.eigvalsh(R.explicit_matrix(p, 3))
+    ctx = _ctx(E, pr)
+    try:
+        om, rn, it, st = E.eaadc_davidson(ctx, 2, tol=1e-10)
+        assert np.abs(om[0] - ref[:2]).max() <= 1e-10
+    finally:
+        E.eaadc_destroy(ctx)
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(GOLD, "canonical-200.npz")), reason="golden file missing")
+@pytest.mark.parametrize("order", [2, 3])
+def test_canonical_200_fp64_against_oracle(E, order):
+    """o=20, v=200, naux=600, 4 roots: FP64 GPU Davidson vs the oracle to 1e-8 Eh."""
+    g = np.load(os.path.join(GOLD, "canonical-200.npz"))
+    pr = config_problem("canonical-200")
+    ctx = _ctx(E, pr, order)
+    try:
+        m11 = E.eaadc_get_m11(ctx, 0)
+        ref = g[f"m11_{order}"]
+        assert np.abs(m11 - ref).max() <= 1e-11 * np.abs(ref).max()
+        s = E.eaadc_sigma_host(ctx, 0, g[f"probe{order}"][None])
+        sref = g[f"sigma_probe{order}"]
+        assert np.abs(s[0] - sref).max() <= 1e-11 * np.abs(sref).max()
+        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-7, max_sub=40)
+        assert st == 0
+        assert np.abs(om[0] - g[f"omega{order}"]).max() <= 1e-8
+    finally:
+        E.eaadc_destroy(ctx)
