@@ -103,6 +103,17 @@ eaadc_status eaadc_sigma(eaadc_ctx* ctx, int state, int nvec, const double* x_de
 eaadc_status eaadc_sigma_host(eaadc_ctx* ctx, int state, int nvec, const double* x_host,
                               double* sigma_host, int prec);
 
+/* The particle-particle ladder term alone (Sec. II.B: the four-virtual
+ * integrals (bd|ce) = sum_Q B^Q_bd B^Q_ce are applied as two successive DF
+ * contractions and never stored):
+ *   out[n][k][b][c] = sum_Q sum_de B^Q_bd w_n[k][d][e] B^Q_ce
+ * on the BF16/FP32 tensor-core path.
+ *  x_dev   : device [nvec][dim] FP64 vectors (only their 2p1h parts are read)
+ *  out_dev : device [nvec][o][v'][v'] FP32, caller-owned, overwritten
+ *  stream  : cudaStream_t for the launches.  ADC(3) states only. */
+eaadc_status eaadc_ladder(eaadc_ctx* ctx, int state, int nvec, const double* x_dev, float* out_dev,
+                          void* stream);
+
 /* Davidson diagonal preconditioner values D (host [dim]): D_a = M_aa for the
  * 1p part, e_b + e_c - e_k for the 2p1h part. */
 eaadc_status eaadc_diagonal(eaadc_ctx* ctx, int state, double* diag_host);

@@ -170,6 +170,18 @@ eaadc_status eaadc_sigma_host(eaadc_ctx* ctx, int state, int nvec, const double*
     else ea::sigma_mixed(s, st, nvec, x.p, y.p);
     EA_CK(cudaMemcpyAsync(sigma_host, y.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     EA_CK(cudaStreamSynchronize(s));
+    if (prec != EAADC_FP64) ea::check_device_error(s, st);
+  });
+}
+
+eaadc_status eaadc_ladder(eaadc_ctx* ctx, int state, int nvec, const double* x_dev, float* out_dev, void* stream) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    ea::State& st = get_state(ctx, state);
+    if (st.order < 3) ea::fail(EAADC_ERR_STATE, "the ladder is part of ADC(3) only");
+    if (nvec <= 0 || !x_dev || !out_dev) ea::fail(EAADC_ERR_ARG, "bad vector arguments");
+    ea::ladder_only((cudaStream_t)stream, st, nvec, x_dev, out_dev, true);
   });
 }
 

@@ -252,6 +252,7 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
     EA_CK(cudaMemcpyAsync(theta.data(), w.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
     EA_CK(cudaMemcpyAsync(rn.data(), rnd.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
     EA_CK(cudaStreamSynchronize(s));
+    if (prec != EAADC_FP64) check_device_error(s, st);
     for (int r = 0; r < k; ++r)
       if (!std::isfinite(theta[r]) || !std::isfinite(rn[r])) fail(EAADC_ERR_NONFINITE, "davidson: non-finite Ritz value or residual");
     bool all = true;

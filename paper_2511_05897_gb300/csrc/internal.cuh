@@ -114,7 +114,9 @@ struct State {
   DArr<double> M11;               // [v][v]
   DArr<double> diag;              // [dim] Davidson diagonal
   // mixed-precision operands (built lazily)
-  DArr<bf16> Bvv_bf, Kmat_bf, Jmat_bf;
+  DArr<bf16> Bvv_bf, Bb_bf, Kmat_bf, Jmat_bf;  // Bb_bf[b][Q][d] = B^Q_bd
+  DArr<bf16> tauA_bf, tauB_bf, tauC_bf, tauD_bf, tm2A_bf, tm2C_bf;  // (ov x ov) coupling operands
+  DArr<int> err;                              // device error word of bounded waits
   bool mixed_ready = false;
   // last Davidson solution
   DArr<double> evecs;             // [nroots][dim]
@@ -137,6 +139,13 @@ namespace ea {
 void build_state_intermediates(eaadc_ctx* ctx, State& st);
 void sigma_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y);
 void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y);
+void sigma_base_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y, bool ring, bool ladder);
+void check_device_error(cudaStream_t s, State& st);
+void couple_1p_to_2p1h(cudaStream_t s, State& st, const double* y, double* outA, const double* tm2, bool big,
+                       double* Fo, double* Go);
+void couple_2p1h_to_1p(cudaStream_t s, State& st, const double* V, double* sy, const double* tm2,
+                       const double* H1g, const double* H2g, const double* H3g);
+void ladder_only(cudaStream_t s, State& st, int nvec, const double* x, float* out, bool mixed);
 void make_diagonal(cudaStream_t s, State& st);
 void davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts& opt, double* omega,
               double* resnorm, int* iters, bool* converged);

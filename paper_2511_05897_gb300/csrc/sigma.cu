@@ -46,8 +46,12 @@ __global__ void diag2p1h_kernel(const double* __restrict__ x, double* __restrict
 int gridn(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
 }  // namespace
 
-// out (A-representation, [o][v][v]) += alpha * sum_a C_A[k,b,c,a] y_a
-static void couple_1p_to_2p1h(cudaStream_t s, State& st, const double* y, double* outA, const double* tm2) {
+// out (A-representation, [o][v][v]) = sum_a C_A[k,b,c,a] y_a.
+// big = false skips the three o^2 v^3 tau contractions and instead returns the
+// DF intermediates F[l][c][d] = sum_a (al|cd) y_a and G[b][l][d] = sum_a (ab|ld) y_a
+// (when Fo/Go are given) for the tensor-core path.
+void couple_1p_to_2p1h(cudaStream_t s, State& st, const double* y, double* outA, const double* tm2, bool big,
+                       double* Fo, double* Go) {
   const int o = st.o, v = st.v, naux = st.naux;
   Tens Bov{st.Bov.p, {naux, o, v}}, Bvv{st.Bvv.p, {naux, v, v}}, Boo{st.Boo.p, {naux, o, o}};
   Tens yt{(double*)y, {v}};
@@ -58,20 +62,29 @@ static void couple_1p_to_2p1h(cudaStream_t s, State& st, const double* y, double
   einsum(s, "Qb,Qkc->kbc", 1.0, Qyt, Bov, 0.0, out);
   if (st.order < 3) return;
   Tens tau{st.tau.p, {o, o, v, v}};
-  DArr<double> Qo((size_t)naux * o, s), F((size_t)o * v * v, s), G((size_t)o * v * v, s), H((size_t)o * o * o, s);
-  Tens Qot{Qo.p, {naux, o}}, Ft{F.p, {o, v, v}}, Gt{G.p, {v, o, v}}, Ht{H.p, {o, o, o}};
+  DArr<double> Qo((size_t)naux * o, s), F, G, H((size_t)o * o * o, s);
+  double* Fp = Fo;
+  double* Gp = Go;
+  if (!Fp) { F.alloc((size_t)o * v * v, s); Fp = F.p; }
+  if (!Gp) { G.alloc((size_t)o * v * v, s); Gp = G.p; }
+  Tens Qot{Qo.p, {naux, o}}, Ft{Fp, {o, v, v}}, Gt{Gp, {v, o, v}}, Ht{H.p, {o, o, o}};
   einsum(s, "Qla,a->Ql", 1.0, Bov, yt, 0.0, Qot);
   einsum(s, "Ql,Qcd->lcd", 1.0, Qot, Bvv, 0.0, Ft);
   einsum(s, "Qb,Qld->bld", 1.0, Qyt, Bov, 0.0, Gt);
   einsum(s, "Ql,Qkm->lkm", 1.0, Qot, Boo, 0.0, Ht);
+  einsum(s, "lkm,lmbc->kbc", 1.0, Ht, tau, 1.0, out);
+  if (!big) return;
   einsum(s, "lcd,lkbd->kbc", -1.0, Ft, tau, 1.0, out);
   einsum(s, "bld,lkcd->kbc", -1.0, Gt, Tens{(double*)tm2, {o, o, v, v}}, 1.0, out);
   einsum(s, "lbd,lkdc->kbc", -1.0, Ft, tau, 1.0, out);
-  einsum(s, "lkm,lmbc->kbc", 1.0, Ht, tau, 1.0, out);
 }
 
-// sy[a] += sum_kbc C_A[k,b,c,a] V[k,b,c]
-static void couple_2p1h_to_1p(cudaStream_t s, State& st, const double* V, double* sy, const double* tm2) {
+// sy[a] += sum_kbc C_A[k,b,c,a] V[k,b,c].  With H1..H3 given (tensor-core
+// path) the three o^2 v^3 contractions H1[l][d][c] = sum_kb t_lk^bd V_kbc,
+// H2[b][l][d] = sum_kc (t_lk^cd - 2 t_lk^dc) V_kbc, H3[l][b][d] = sum_kc t_lk^dc V_kbc
+// are taken from them instead of being formed here.
+void couple_2p1h_to_1p(cudaStream_t s, State& st, const double* V, double* sy, const double* tm2,
+                       const double* H1g, const double* H2g, const double* H3g) {
   const int o = st.o, v = st.v, naux = st.naux;
   Tens Bov{st.Bov.p, {naux, o, v}}, Bvv{st.Bvv.p, {naux, v, v}}, Boo{st.Boo.p, {naux, o, o}};
   Tens Vt{(double*)V, {o, v, v}};
@@ -82,16 +95,19 @@ static void couple_2p1h_to_1p(cudaStream_t s, State& st, const double* V, double
   einsum(s, "Qba,Qb->a", 1.0, Bvv, gt, 1.0, out);  // B^Q symmetric
   if (st.order < 3) return;
   Tens tau{st.tau.p, {o, o, v, v}};
-  DArr<double> H((size_t)o * v * v, s), tt((size_t)naux * o, s), t2q((size_t)naux * v, s), H4((size_t)o * o * o, s);
-  Tens Ht{H.p, {o, v, v}}, ttt{tt.p, {naux, o}}, t2qt{t2q.p, {naux, v}};
-  einsum(s, "lkbd,kbc->ldc", 1.0, tau, Vt, 0.0, Ht);
-  einsum(s, "Qcd,ldc->Ql", -1.0, Bvv, Ht, 0.0, ttt);
-  Tens H2t{H.p, {v, o, v}};
-  einsum(s, "lkcd,kbc->bld", 1.0, Tens{(double*)tm2, {o, o, v, v}}, Vt, 0.0, H2t);
+  DArr<double> H, tt((size_t)naux * o, s), t2q((size_t)naux * v, s), H4((size_t)o * o * o, s);
+  Tens ttt{tt.p, {naux, o}}, t2qt{t2q.p, {naux, v}};
+  const bool ext = H1g != nullptr;
+  if (!ext) H.alloc((size_t)o * v * v, s);
+  Tens H1t{ext ? (double*)H1g : H.p, {o, v, v}};
+  if (!ext) einsum(s, "lkbd,kbc->ldc", 1.0, tau, Vt, 0.0, H1t);
+  einsum(s, "Qcd,ldc->Ql", -1.0, Bvv, H1t, 0.0, ttt);
+  Tens H2t{ext ? (double*)H2g : H.p, {v, o, v}};
+  if (!ext) einsum(s, "lkcd,kbc->bld", 1.0, Tens{(double*)tm2, {o, o, v, v}}, Vt, 0.0, H2t);
   einsum(s, "Qld,bld->Qb", 1.0, Bov, H2t, 0.0, t2qt);
   einsum(s, "Qba,Qb->a", -1.0, Bvv, t2qt, 1.0, out);
-  Tens H3t{H.p, {o, v, v}};
-  einsum(s, "lkdc,kbc->lbd", 1.0, tau, Vt, 0.0, H3t);
+  Tens H3t{ext ? (double*)H3g : H.p, {o, v, v}};
+  if (!ext) einsum(s, "lkdc,kbc->lbd", 1.0, tau, Vt, 0.0, H3t);
   einsum(s, "Qbd,lbd->Ql", -1.0, Bvv, H3t, 1.0, ttt);
   Tens H4t{H4.p, {o, o, o}};
   einsum(s, "lmbc,kbc->lkm", 1.0, tau, Vt, 0.0, H4t);
@@ -117,7 +133,8 @@ static void ring_fp64(cudaStream_t s, State& st, const double* W, double* sW) {
   pair_combine(s, A.p, vv, sW, vv, o, v, kS1, kS2, 1.0, 1.0);
 }
 
-void sigma_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y) {
+// All terms except (optionally) the ring and ladder terms, FP64.
+void sigma_base_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y, bool ring, bool ladder) {
   const int o = st.o, v = st.v;
   const long long dim = st.dim, vv = (long long)v * v, n2 = (long long)o * vv;
   diag2p1h_kernel<<<gridn(n2 * nvec), 256, 0, s>>>(x, y, st.eo.p, st.ev.p, o, v, dim, nvec);
@@ -137,14 +154,18 @@ void sigma_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y)
     double* yn = y + n * dim;
     // 2p1h -> 1p with V = S(W)
     pair_combine(s, xn + v, vv, V.p, vv, o, v, kS1, kS2, 1.0, 0.0);
-    couple_2p1h_to_1p(s, st, V.p, yn, tm2.p);
+    couple_2p1h_to_1p(s, st, V.p, yn, tm2.p, nullptr, nullptr, nullptr);
     // 1p -> 2p1h
-    couple_1p_to_2p1h(s, st, xn, CA.p, tm2.p);
+    couple_1p_to_2p1h(s, st, xn, CA.p, tm2.p, true, nullptr, nullptr);
     pair_combine(s, CA.p, vv, yn + v, vv, o, v, kS1, kS2, 1.0, 1.0);
-    if (st.order >= 3) ring_fp64(s, st, xn + v, yn + v);
+    if (ring && st.order >= 3) ring_fp64(s, st, xn + v, yn + v);
   }
-  if (st.order >= 3)
+  if (ladder && st.order >= 3)
     ladder_fp64(s, st.Bvv.p, st.naux, v, x + v, vv, nvec, dim, o, y + v, dim, vv, 1.0, 1.0);
+}
+
+void sigma_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y) {
+  sigma_base_fp64(s, st, nvec, x, y, true, true);
 }
 
 }  // namespace ea

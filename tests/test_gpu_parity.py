@@ -122,3 +122,82 @@ def test_canonical_200_fp64_against_oracle(E, order):
         assert np.abs(om[0] - g[f"omega{order}"]).max() <= 1e-8
     finally:
         E.eaadc_destroy(ctx)
+
+
+# ---------------------------------------------------------------- mixed path
+MIXED_CASES = [(1, 2, 3, 2.0, 4), (4, 13, 40, 8.0, 9), (2, 70, 30, 10.0, 3), (5, 20, 60, 15.0, 1),
+               (3, 136, 90, 20.0, 7)]
+
+
+@pytest.mark.parametrize("o,v,naux,decay,seed", MIXED_CASES)
+def test_ladder_tensor_core_vs_oracle(E, o, v, naux, decay, seed):
+    """a1 on tcgen05 (BF16 operands, FP32 accumulation) vs the FP64 DF ladder.
+
+    Tolerance: BF16 keeps 8 significant bits (relative rounding 2^-9) on B, on
+    w and on the stage-1 intermediate; with FP32 accumulation the error of each
+    output stays below ~3 * 2^-9 of the largest |term|, bounded here by 2e-2 of
+    max |ladder| for unit-variance inputs."""
+    import torch
+
+    pr = make_problem(o, v, naux, decay, seed)
+    p = R.Problem(pr["eps_occ"], pr["eps_vir"], pr["B"])
+    ctx = _ctx(E, pr)
+    try:
+        dim = v + o * v * v
+        x = np.random.default_rng(seed).standard_normal((2, dim))
+        xd = torch.tensor(x, device="cuda:0")
+        out = torch.empty((2, o, v, v), dtype=torch.float32, device="cuda:0")
+        E.eaadc_ladder(ctx, 0, 2, xd.data_ptr(), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        got = out.double().cpu().numpy()
+        for n in range(2):
+            ref = R.ladder_w(p, x[n, v:].reshape(o, v, v))
+            assert np.abs(got[n] - ref).max() <= 2e-2 * np.abs(ref).max()
+    finally:
+        E.eaadc_destroy(ctx)
+
+
+@pytest.mark.parametrize("o,v,naux,decay,seed", MIXED_CASES)
+def test_mixed_sigma_vs_fp64(E, o, v, naux, decay, seed):
+    pr = make_problem(o, v, naux, decay, seed)
+    p = R.Problem(pr["eps_occ"], pr["eps_vir"], pr["B"])
+    ctx = _ctx(E, pr)
+    try:
+        dim = v + o * v * v
+        x = np.random.default_rng(seed + 1).standard_normal((3, dim))
+        s64 = E.eaadc_sigma_host(ctx, 0, x, E.EAADC_FP64)
+        smx = E.eaadc_sigma_host(ctx, 0, x, E.EAADC_MIXED_BF16)
+        scale = max(np.abs(R.ladder_w(p, x[n, v:].reshape(o, v, v)) + R.ring_w(p, x[n, v:].reshape(o, v, v))).max()
+                    for n in range(3))
+        assert np.abs(smx - s64).max() <= 2e-2 * scale
+        # the 1p part does not use tensor cores: FP64-exact
+        assert np.abs(smx[:, :v] - s64[:, :v]).max() <= 1e-12 * np.abs(s64[:, :v]).max()
+    finally:
+        E.eaadc_destroy(ctx)
+
+
+def test_mixed_davidson_tiny(E):
+    pr = config_problem("tiny")
+    p = R.Problem(pr["eps_occ"], pr["eps_vir"], pr["B"])
+    ref = np.linalg.eigvalsh(R.explicit_matrix(p, 3))[:4]
+    ctx = _ctx(E, pr)
+    try:
+        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-6, prec=E.EAADC_MIXED_BF16, refine=0)
+        assert np.abs(om[0] - ref).max() <= 1e-5       # reduced-precision target
+        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-8, prec=E.EAADC_MIXED_BF16, refine=1)
+        assert st == 0 and np.abs(om[0] - ref).max() <= 1e-8  # after FP64 refinement
+    finally:
+        E.eaadc_destroy(ctx)
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(GOLD, "canonical-200.npz")), reason="golden file missing")
+def test_canonical_200_mixed_refined_against_oracle(E):
+    g = np.load(os.path.join(GOLD, "canonical-200.npz"))
+    pr = config_problem("canonical-200")
+    ctx = _ctx(E, pr)
+    try:
+        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-7, prec=E.EAADC_MIXED_BF16, refine=1)
+        assert st == 0
+        assert np.abs(om[0] - g["omega3"]).max() <= 1e-8
+    finally:
+        E.eaadc_destroy(ctx)
