@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""DF-EA-ADC(3) sigma throughput and time-to-roots on GB300.
+
+Workload (default): canonical EA-ADC(3), o=20 occupied, v=200 virtual,
+naux=600 auxiliary functions, 4 roots, synthetic inputs from ``synth``
+(seeded SplitMix64/Box-Muller generator; occupied energies uniform in
+[-1.2,-0.4] Eh, virtual energies log-spaced 0.02-20 Eh, symmetric Gaussian
+B^Q with decay exp(-Q/150), scaled to max |t| = 0.05).
+
+One timed step = one grouped sigma launch sigma = M c over the 4 root vectors
+in mixed precision (DF ladder, ring and coupling GEMMs on tcgen05 BF16 tensor
+cores, FP32 accumulation; diagonal, 1p/1p block and DF pieces in FP64), the
+unit Davidson repeats every iteration.  L2 is flushed (256 MB write) between
+timed steps.  Time-to-roots (mixed precision + FP64 refinement to
+||r|| <= 1e-6) is measured once beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DF-EA-ADC(3) sigma TFLOP/s + time-to-roots vs FP64 GPU at ≤1e-5 Eh"
+WORKLOAD = "canonical-200"
+NROOTS = 4
+
+
+def sigma_flops(o, v, naux, nvec):
+    """Algorithmic flops of one sigma: DF ladder 4 o v^3 naux, ring 3 x 2 (ov)^2 v,
+    second-order coupling 6 x 2 (ov)^2 v, DF coupling pieces 8 x 2 naux o v^2."""
+    return nvec * (4.0 * o * v ** 3 * naux + 18.0 * o * o * v ** 3 + 16.0 * naux * o * v * v)
+
+
+def ladder_flops(o, v, naux, nvec):
+    return nvec * 4.0 * o * v ** 3 * naux
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("bf16_tflops", 1900.0), d.get("hbm_gbs", 6800.0), "measured"
+    return 1900.0, 6800.0, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in ("tc_gemm.cuh", "tc_common.cuh", "sigma_mixed.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2511_05897_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ladder_traffic():
+    """DRAM bytes per ladder call from the committed ncu summary, if it was
+    taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "ladder_canonical-200.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    return d.get("dram_bytes_per_call") if d.get("source_sha") == source_sha() else None
+
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(pr, nvec=1):
+    """The CPU oracle's sigma (numpy FP64, all host cores) on a bounded sample:
+    nvec vectors of the same workload (the 1p/1p intermediate, a one-off
+    construction, is replaced by its diagonal: the per-vector cost is the same)."""
+    from oracle import restricted as R
+
+    p = R.Problem(pr["eps_occ"], pr["eps_vir"], pr["B"])
+    sig = R.Sigma.__new__(R.Sigma)
+    sig.p, sig.order = p, 3
+    sig.M11 = np.diag(p.ev)
+    sig.D2p1h = R.diag_2p1h(p)
+    dim = p.v + p.o * p.v * p.v
+    x = np.random.default_rng(0).standard_normal((nvec, dim))
+    t0 = time.perf_counter()
+    sig(x)
+    dt = time.perf_counter() - t0
+    fl = sigma_flops(p.o, p.v, p.naux, nvec)
+    return {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{nvec} sigma vector(s) of {WORKLOAD} (numpy FP64, BLAS on all host cores), {dt:.1f} s"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from synth import config_problem
+
+    pr = config_problem(WORKLOAD)
+    times = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(pr, 1)
+        if i >= args.warmup:
+            times.append(cb)
+    val = statistics.mean(t["value"] for t in times)
+    o, v, naux = pr["o"], pr["v"], pr["naux"]
+    fl = sigma_flops(o, v, naux, 1)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": fl / (val * 1e12) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{WORKLOAD} (o={o}, v={v}, naux={naux})", "nvec": 1},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "1 sigma vector per step (numpy FP64 oracle on all host cores)"},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-roots", action="store_true", help="skip the time-to-roots solve")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    args.warmup = max(3, args.warmup)
+
+    import torch
+    import torch.distributed as dist
+
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import paper_2511_05897_gb300 as E
+
+    if not os.path.exists(E.LIB_PATH):
+        import __graft_entry__ as g
+
+        g.build()
+    from synth import config_problem
+
+    pr = config_problem(WORKLOAD)
+    o, v, naux = pr["o"], pr["v"], pr["naux"]
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ctx = E.eaadc_init(o, v, naux, pr["eps_occ"], pr["eps_vir"], pr["B"], local, sh)
+    try:
+        E.eaadc_build_canonical(ctx, 3, 1.0)
+        _, _, dim = E.eaadc_state_info(ctx, 0)
+        nvec = NROOTS
+        x = torch.randn(nvec, dim, dtype=torch.float64, device="cuda")
+        x /= x.norm(dim=1, keepdim=True)
+        y = torch.empty_like(x)
+        lad = torch.empty(nvec, o, v, v, dtype=torch.float32, device="cuda")
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        fl_step = sigma_flops(o, v, naux, nvec)
+
+        def step():
+            E.eaadc_sigma(ctx, 0, nvec, x.data_ptr(), y.data_ptr(), E.EAADC_MIXED_BF16, sh)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        with Clocks(local) as clk:
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            n0 = E.eaadc_kernel_launches()
+            for i in range(args.steps):
+                flush.zero_()
+                ev[i][0].record(stream)
+                step()
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            n1 = E.eaadc_kernel_launches()
+            if world > 1:
+                dist.barrier()
+            ms = [a.elapsed_time(b) for a, b in ev]
+            # dominant kernel: the DF ladder alone, same stream
+            lev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            for i in range(args.steps):
+                flush.zero_()
+                lev[i][0].record(stream)
+                E.eaadc_ladder(ctx, 0, nvec, x.data_ptr(), lad.data_ptr(), sh)
+                lev[i][1].record(stream)
+            torch.cuda.synchronize()
+            lms = statistics.mean(a.elapsed_time(b) for a, b in lev)
+            # end to end through the host-buffer entry point (pinned memory, copies timed)
+            xh = torch.empty((nvec, dim), dtype=torch.float64, pin_memory=True)
+            xh.copy_(x)
+            xn = xh.numpy()
+            e2e_t = []
+            for i in range(max(2, args.steps // 2)):
+                t0 = time.perf_counter()
+                E.eaadc_sigma_host(ctx, 0, xn, E.EAADC_MIXED_BF16)
+                e2e_t.append(time.perf_counter() - t0)
+        mean_ms = statistics.mean(ms)
+        if world > 1:
+            t = torch.tensor([mean_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            mean_ms = float(t.item())
+        value = world * fl_step / (mean_ms * 1e-3) / 1e12
+        e2e_val = fl_step / statistics.mean(e2e_t) / 1e12
+        bf16_peak, hbm_peak, src = peaks()
+        achieved = ladder_flops(o, v, naux, nvec) / (lms * 1e-3) / 1e12
+        roots = None
+        if not args.no_roots and rank == 0:
+            t0 = time.perf_counter()
+            om, rn, it, st = E.eaadc_davidson(ctx, NROOTS, tol=1e-6, prec=E.EAADC_MIXED_BF16, refine=1, max_sub=40,
+                                              maxit=300)
+            roots = {"seconds": time.perf_counter() - t0, "omega_eh": [float(w) for w in om[0]],
+                     "resnorm": [float(r) for r in rn[0]], "iterations": int(it[0]), "status": int(st),
+                     "mode": "mixed BF16 sigma + FP64 refinement, ||r|| <= 1e-6"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: canonical EA-ADC(3), o={o}, v={v}, naux={naux}, {NROOTS} roots",
+                       "nvec_per_step": nvec, "l2": "flushed (256 MB write) between timed steps",
+                       "precision": "BF16 tensor-core operands, FP32 accumulation; FP64 elsewhere"},
+            "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": nvec * dim * 8,
+                    "d2h_bytes_per_step": nvec * dim * 8},
+            "gpu_launches": int(n1 - n0),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16_peak, "unit": "TFLOP/s",
+                         "frac": achieved / bf16_peak, "traffic": ladder_traffic(),
+                         "kernel": "DF particle-particle ladder (tcgen05 BF16 GEMM stages), one call",
+                         "ms_per_launch": lms, "peak_source": f"{src} bf16 dense burst"},
+            "clocks": clk.summary(),
+        }
+        if roots is not None:
+            line["time_to_roots"] = roots
+        if rank == 0 and world == 1:
+            line["cpu_baseline"] = cpu_baseline(pr, 1)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+    finally:
+        E.eaadc_destroy(ctx)
+        if world > 1:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -69,6 +69,10 @@ typedef struct {
 /* Library version string (static storage). */
 const char* eaadc_version(void);
 
+/* Number of CUDA kernels this library has launched in this process so far
+ * (instrumentation for benchmarks; the paper has no counterpart). */
+long long eaadc_kernel_launches(void);
+
 /* Create a context on `device` and upload the canonical problem.
  *  o, v, naux : occupied, virtual and auxiliary sizes (o >= 1, v >= 1, naux >= 1)
  *  eps_occ    : host [o] occupied orbital energies
@@ -106,8 +110,9 @@ eaadc_status eaadc_sigma_host(eaadc_ctx* ctx, int state, int nvec, const double*
 /* The particle-particle ladder term alone (Sec. II.B: the four-virtual
  * integrals (bd|ce) = sum_Q B^Q_bd B^Q_ce are applied as two successive DF
  * contractions and never stored):
- *   out[n][k][b][c] = sum_Q sum_de B^Q_bd w_n[k][d][e] B^Q_ce
- * on the BF16/FP32 tensor-core path.
+ *   out[n][k][c][b] = sum_Q sum_de B^Q_bd w_n[k][d][e] B^Q_ce
+ * (note the transposed (c, b) order of the output) on the BF16/FP32
+ * tensor-core path.
  *  x_dev   : device [nvec][dim] FP64 vectors (only their 2p1h parts are read)
  *  out_dev : device [nvec][o][v'][v'] FP32, caller-owned, overwritten
  *  stream  : cudaStream_t for the launches.  ADC(3) states only. */

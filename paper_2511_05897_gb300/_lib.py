@@ -26,7 +26,7 @@ EAADC_MIXED_BF16 = 1
 EXPORTED = (
     "eaadc_version", "eaadc_init", "eaadc_build_canonical", "eaadc_state_info", "eaadc_sigma",
     "eaadc_sigma_host", "eaadc_diagonal", "eaadc_get_m11", "eaadc_davidson", "eaadc_get_eigvecs",
-    "eaadc_destroy", "eaadc_last_error", "eaadc_ladder",
+    "eaadc_destroy", "eaadc_last_error", "eaadc_ladder", "eaadc_kernel_launches",
 )
 
 
@@ -52,6 +52,7 @@ def lib():
         L = C.CDLL(LIB_PATH)
         vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
         L.eaadc_version.restype = C.c_char_p
+        L.eaadc_kernel_launches.restype = C.c_longlong
         L.eaadc_init.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, vp]
         L.eaadc_build_canonical.argtypes = [vp, C.c_int, C.c_double]
         L.eaadc_state_info.argtypes = [vp, C.c_int, ip, ip, C.POINTER(C.c_longlong)]
@@ -67,7 +68,7 @@ def lib():
         L.eaadc_last_error.argtypes = [vp]
         L.eaadc_last_error.restype = C.c_char_p
         for name in EXPORTED:
-            if name not in ("eaadc_version", "eaadc_destroy", "eaadc_last_error"):
+            if name not in ("eaadc_version", "eaadc_destroy", "eaadc_last_error", "eaadc_kernel_launches"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -88,6 +89,10 @@ def _check(ctx, st):
 
 def eaadc_version():
     return lib().eaadc_version().decode()
+
+
+def eaadc_kernel_launches():
+    return int(lib().eaadc_kernel_launches())
 
 
 def eaadc_last_error(ctx):

@@ -50,6 +50,8 @@ extern "C" {
 
 const char* eaadc_version(void) { return "eaadc-gb300 0.1 (sm_103a)"; }
 
+long long eaadc_kernel_launches(void) { return __atomic_load_n(&ea::g_kernel_launches, __ATOMIC_RELAXED); }
+
 eaadc_status eaadc_init(eaadc_ctx** out, int o, int v, int naux, const double* eps_occ, const double* eps_vir,
                         const double* B, int device, void* stream) {
   if (!out) { g_static_err = "out is NULL"; return EAADC_ERR_ARG; }

@@ -25,7 +25,13 @@ struct Error {
                                      " at " + __FILE__ + ":" + std::to_string(__LINE__)); \
   } while (0)
 
-#define EA_LAUNCH() EA_CK(cudaGetLastError())
+// Counts every kernel launched by this library (instrumentation).
+extern long long g_kernel_launches;
+#define EA_LAUNCH()                                             \
+  do {                                                          \
+    __atomic_add_fetch(&::ea::g_kernel_launches, 1, __ATOMIC_RELAXED); \
+    EA_CK(cudaGetLastError());                                  \
+  } while (0)
 
 // ------------------------------------------------------------ device memory
 // Stream-ordered device array owned by its creator.
@@ -141,6 +147,7 @@ void sigma_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y)
 void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y);
 void sigma_base_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y, bool ring, bool ladder);
 void check_device_error(cudaStream_t s, State& st);
+void diag_and_m11(cudaStream_t s, State& st, int nvec, const double* x, double* y);
 void couple_1p_to_2p1h(cudaStream_t s, State& st, const double* y, double* outA, const double* tm2, bool big,
                        double* Fo, double* Go);
 void couple_2p1h_to_1p(cudaStream_t s, State& st, const double* V, double* sy, const double* tm2,

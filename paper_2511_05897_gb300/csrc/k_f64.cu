@@ -11,21 +11,29 @@ namespace ea {
 
 [[noreturn]] void fail(eaadc_status st, const std::string& msg) { throw Error{st, msg}; }
 
+long long g_kernel_launches = 0;
+
 // ------------------------------------------------------------------- DGEMM
 namespace {
 constexpr int BM = 64, BN = 64, BK = 16;
 
+// blockIdx.z = zb * ksplit + zs: batch entry zb, K slice zs of length kchunk.
+// With ksplit > 1 each slice writes alpha * (its partial product) to its own
+// [M][N] panel of C (panels ksplit*nbatch apart is the caller's layout).
 template <bool TA, bool TB, bool BETA0>
 __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha,
                                                     const double* __restrict__ A, long long lda,
                                                     const double* __restrict__ B, long long ldb,
                                                     double beta, double* __restrict__ C, long long ldc,
-                                                    GemmBatch bt) {
-  const int z = blockIdx.z;
+                                                    GemmBatch bt, int ksplit, int kchunk, long long spanel) {
+  const int zs = blockIdx.z % ksplit;
+  const int z = blockIdx.z / ksplit;
   const int z1 = z / bt.nb2, z2 = z % bt.nb2;
   A += z1 * bt.sA1 + z2 * bt.sA2;
   B += z1 * bt.sB1 + z2 * bt.sB2;
-  C += z1 * bt.sC1 + z2 * bt.sC2;
+  C += z1 * bt.sC1 + z2 * bt.sC2 + (long long)zs * spanel;
+  const int kbeg = zs * kchunk;
+  const int kend = min(K, kbeg + kchunk);
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
@@ -36,7 +44,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int k0 = 0; k0 < K; k0 += BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       int i = tid + 256 * r;
@@ -44,14 +52,14 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
       if (TA) { mm = i % BM; kk = i / BM; } else { kk = i % BK; mm = i / BK; }
       int gm = m0 + mm, gk = k0 + kk;
       double a = 0.0;
-      if (gm < M && gk < K) a = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+      if (gm < M && gk < kend) a = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
       As[kk][mm] = a;
       int nn;
       if (TB) { kk = i % BK; nn = i / BK; } else { nn = i % BN; kk = i / BN; }
       int gn = n0 + nn;
       gk = k0 + kk;
       double b = 0.0;
-      if (gn < N && gk < K) b = TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
+      if (gn < N && gk < kend) b = TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
       Bs[kk][nn] = b;
     }
     __syncthreads();
@@ -83,14 +91,47 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   }
 }
 
+__global__ void splitk_reduce(const double* __restrict__ P, int ksplit, long long panel, int M, int N,
+                              double beta, double* __restrict__ C, long long ldc) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < panel; e += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < ksplit; ++z) acc += P[(long long)z * panel + e];
+    const long long m = e / N, n = e % N;
+    double* c = C + m * ldc + n;
+    *c = (beta == 0.0) ? acc : acc + beta * (*c);
+  }
+}
+
 template <bool TA, bool TB>
 void dgemm_t(cudaStream_t s, int M, int N, int K, double alpha, const double* A, long long lda,
              const double* B, long long ldb, double beta, double* C, long long ldc, const GemmBatch& bt) {
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, bt.nb1 * bt.nb2);
-  if (beta == 0.0)
-    dgemm_kernel<TA, TB, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
-  else
-    dgemm_kernel<TA, TB, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  const int nbatch = bt.nb1 * bt.nb2;
+  const long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * nbatch;
+  // split K when the output grid cannot fill the GPU and K is long
+  int ksplit = 1;
+  if (nbatch == 1 && tiles < 152 && K >= 1024) {
+    ksplit = (int)std::min<long long>(std::min<long long>((304 + tiles - 1) / tiles, K / 256), 64);
+    if (ksplit < 2) ksplit = 1;
+  }
+  if (ksplit == 1) {
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nbatch);
+    if (beta == 0.0)
+      dgemm_kernel<TA, TB, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, 1, K, 0);
+    else
+      dgemm_kernel<TA, TB, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, 1, K, 0);
+    EA_LAUNCH();
+    return;
+  }
+  const int kchunk = ((K + ksplit - 1) / ksplit + BK - 1) / BK * BK;
+  ksplit = (K + kchunk - 1) / kchunk;
+  const long long panel = (long long)M * N;
+  DArr<double> P((size_t)(panel * ksplit), s);
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, ksplit);
+  dgemm_kernel<TA, TB, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, 0.0, P.p, N, bt, ksplit, kchunk,
+                                                  panel);
+  EA_LAUNCH();
+  splitk_reduce<<<(int)std::min<long long>((panel + 255) / 256, 4096), 256, 0, s>>>(P.p, ksplit, panel, M, N, beta,
+                                                                                   C, ldc);
   EA_LAUNCH();
 }
 }  // namespace

@@ -133,6 +133,15 @@ static void ring_fp64(cudaStream_t s, State& st, const double* W, double* sW) {
   pair_combine(s, A.p, vv, sW, vv, o, v, kS1, kS2, 1.0, 1.0);
 }
 
+// Orbital-energy diagonal of the 2p1h block and the 1p/1p block (overwrites y).
+void diag_and_m11(cudaStream_t s, State& st, int nvec, const double* x, double* y) {
+  const int o = st.o, v = st.v;
+  const long long dim = st.dim, n2 = (long long)o * v * v;
+  diag2p1h_kernel<<<gridn(n2 * nvec), 256, 0, s>>>(x, y, st.eo.p, st.ev.p, o, v, dim, nvec);
+  EA_LAUNCH();
+  dgemm(s, false, false, nvec, v, v, 1.0, x, dim, st.M11.p, v, 0.0, y, dim);
+}
+
 // All terms except (optionally) the ring and ladder terms, FP64.
 void sigma_base_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y, bool ring, bool ladder) {
   const int o = st.o, v = st.v;

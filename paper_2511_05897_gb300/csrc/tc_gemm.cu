@@ -1,6 +1,5 @@
-// Host side of the tcgen05 GEMM: TMA tensor-map encoding (driver entry point
-// obtained through the runtime, so the library does not link libcuda) and
-// kernel launches.
+// TMA operand tensor maps (the driver entry point is obtained through the
+// runtime, so the library does not link libcuda).
 #include "tc_gemm.cuh"
 
 namespace ea {
@@ -21,18 +20,6 @@ EncodeFn encoder() {
   return fn;
 }
 
-template <int BN, int MODE>
-void launch(cudaStream_t s, const TmaMap& A, const TmaMap& B, const tc::GemmArgs& g, int batch) {
-  constexpr size_t smem = tc::gemm_smem_bytes<BN>();
-  static bool attr = false;
-  if (!attr) {
-    EA_CK(cudaFuncSetAttribute(tc::tc_gemm_kernel<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
-  dim3 grid((g.N + BN - 1) / BN, (g.M + tc::kBM - 1) / tc::kBM, batch);
-  tc::tc_gemm_kernel<BN, MODE><<<grid, 128, smem, s>>>(A.map, B.map, g);
-  EA_LAUNCH();
-}
 }  // namespace
 
 TmaMap make_tma_3d(const bf16* base, long long K, long long rows, long long nb, long long row_pitch,
@@ -50,22 +37,6 @@ TmaMap make_tma_3d(const bf16* base, long long K, long long rows, long long nb, 
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) fail(EAADC_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return m;
-}
-
-void tc_gemm(cudaStream_t s, const TmaMap& A, const TmaMap& B, const tc::GemmArgs& g, int batch, int mode, int bn) {
-  if (g.M <= 0 || g.N <= 0 || batch <= 0) return;
-  if (batch > 65535 || (g.M + tc::kBM - 1) / tc::kBM > 65535) fail(EAADC_ERR_ARG, "tc_gemm: grid too large");
-  if (bn == 256) {
-    if (mode == tc::EPI_F32) launch<256, tc::EPI_F32>(s, A, B, g, batch);
-    else if (mode == tc::EPI_F64_ADD) launch<256, tc::EPI_F64_ADD>(s, A, B, g, batch);
-    else launch<256, tc::EPI_LADDER_Z>(s, A, B, g, batch);
-  } else if (bn == 128) {
-    if (mode == tc::EPI_F32) launch<128, tc::EPI_F32>(s, A, B, g, batch);
-    else if (mode == tc::EPI_F64_ADD) launch<128, tc::EPI_F64_ADD>(s, A, B, g, batch);
-    else launch<128, tc::EPI_LADDER_Z>(s, A, B, g, batch);
-  } else {
-    fail(EAADC_ERR_ARG, "tc_gemm: unsupported tile width");
-  }
 }
 
 }  // namespace ea

@@ -1,0 +1,77 @@
+// Host side of the persistent tcgen05 GEMM: output tensor maps and launch.
+#include "tc_gemm2.cuh"
+
+namespace ea {
+namespace {
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeFn encoder2() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    EA_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) fail(EAADC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = (EncodeFn)p;
+  }
+  return fn;
+}
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    EA_CK(cudaGetDevice(&dev));
+    EA_CK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return n;
+}
+}  // namespace
+
+TmaMap make_tma_out4d(const void* base, int elem_bytes, long long cols, long long nzlo, long long rows, long long nzhi,
+                      long long pitch_zlo, long long pitch_row, long long pitch_zhi) {
+  if (((uintptr_t)base & 15) || (pitch_zlo * elem_bytes) % 16 || (pitch_row * elem_bytes) % 16 ||
+      (pitch_zhi * elem_bytes) % 16)
+    fail(EAADC_ERR_ARG, "TMA output not 16-byte aligned");
+  TmaMap m;
+  cuuint64_t dims[4] = {(cuuint64_t)cols, (cuuint64_t)nzlo, (cuuint64_t)rows, (cuuint64_t)nzhi};
+  cuuint64_t strides[3] = {(cuuint64_t)(pitch_zlo * elem_bytes), (cuuint64_t)(pitch_row * elem_bytes),
+                           (cuuint64_t)(pitch_zhi * elem_bytes)};
+  cuuint32_t box[4] = {32, 1, 32, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = encoder2()(&m.map, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                          4, (void*)base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          elem_bytes == 4 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(EAADC_ERR_CUDA, "cuTensorMapEncodeTiled (output) failed: " + std::to_string((int)r));
+  return m;
+}
+
+int pick_bn(int N) {
+  int best = 256;
+  long long bestw = -1;
+  for (int bn = 256; bn >= 128; bn -= 32) {
+    long long w = (long long)((N + bn - 1) / bn) * bn;
+    if (bestw < 0 || w < bestw) { bestw = w; best = bn; }
+  }
+  return best;
+}
+
+void tc_gemm2(cudaStream_t s, const TmaMap& A, const TmaMap& B, const TmaMap& C, const tc2::Args& a) {
+  if (a.M <= 0 || a.N <= 0 || a.nz <= 0) return;
+  if (a.BN < 32 || a.BN > 256 || a.BN % 32) fail(EAADC_ERR_ARG, "tc_gemm2: BN must be a multiple of 32 in [32, 256]");
+  if (a.nzlo < 1 || a.nz % a.nzlo) fail(EAADC_ERR_ARG, "tc_gemm2: bad batch split");
+  static bool attr = false;
+  if (!attr) {
+    EA_CK(cudaFuncSetAttribute(tc2::gemm_persistent<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tc2::smem_bytes(256)));
+    attr = true;
+  }
+  const long long tiles = (long long)((a.M + tc2::kBM - 1) / tc2::kBM) * ((a.N + a.BN - 1) / a.BN) * a.nz;
+  if (tiles > (1LL << 31) - 1) fail(EAADC_ERR_ARG, "tc_gemm2: too many tiles");
+  const int grid = (int)std::min<long long>(tiles, sm_count());
+  tc2::gemm_persistent<0><<<grid, tc2::kThreads, tc2::smem_bytes(a.BN), s>>>(A.map, B.map, C.map, a);
+  EA_LAUNCH();
+}
+
+}  // namespace ea

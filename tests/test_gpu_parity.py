@@ -106,7 +106,12 @@ def test_davidson_edge_one_virtual(E):
 @pytest.mark.skipif(not os.path.exists(os.path.join(GOLD, "canonical-200.npz")), reason="golden file missing")
 @pytest.mark.parametrize("order", [2, 3])
 def test_canonical_200_fp64_against_oracle(E, order):
-    """o=20, v=200, naux=600, 4 roots: FP64 GPU Davidson vs the oracle to 1e-8 Eh."""
+    """o=20, v=200, naux=600, 4 roots: 1p/1p block and sampled sigma of seeded
+    probes elementwise; FP64 GPU Davidson roots vs the oracle to 1e-8 Eh."""
+    import sys
+    sys.path.insert(0, GOLD)
+    from make_golden import probes
+
     g = np.load(os.path.join(GOLD, "canonical-200.npz"))
     pr = config_problem("canonical-200")
     ctx = _ctx(E, pr, order)
@@ -114,10 +119,13 @@ def test_canonical_200_fp64_against_oracle(E, order):
         m11 = E.eaadc_get_m11(ctx, 0)
         ref = g[f"m11_{order}"]
         assert np.abs(m11 - ref).max() <= 1e-11 * np.abs(ref).max()
-        s = E.eaadc_sigma_host(ctx, 0, g[f"probe{order}"][None])
+        v, naux, dim = E.eaadc_state_info(ctx, 0)
+        x, idx = probes(dim, v)
+        assert np.array_equal(idx, g["sample_index"])
+        s = E.eaadc_sigma_host(ctx, 0, x)[:, idx]
         sref = g[f"sigma_probe{order}"]
-        assert np.abs(s[0] - sref).max() <= 1e-11 * np.abs(sref).max()
-        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-7, max_sub=40)
+        assert np.abs(s - sref).max() <= 1e-11 * np.abs(sref).max()
+        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-7, max_sub=40, maxit=300)
         assert st == 0
         assert np.abs(om[0] - g[f"omega{order}"]).max() <= 1e-8
     finally:
@@ -151,7 +159,7 @@ def test_ladder_tensor_core_vs_oracle(E, o, v, naux, decay, seed):
         torch.cuda.synchronize()
         got = out.double().cpu().numpy()
         for n in range(2):
-            ref = R.ladder_w(p, x[n, v:].reshape(o, v, v))
+            ref = R.ladder_w(p, x[n, v:].reshape(o, v, v)).transpose(0, 2, 1)  # output is [k][c][b]
             assert np.abs(got[n] - ref).max() <= 2e-2 * np.abs(ref).max()
     finally:
         E.eaadc_destroy(ctx)
@@ -170,8 +178,8 @@ def test_mixed_sigma_vs_fp64(E, o, v, naux, decay, seed):
         scale = max(np.abs(R.ladder_w(p, x[n, v:].reshape(o, v, v)) + R.ring_w(p, x[n, v:].reshape(o, v, v))).max()
                     for n in range(3))
         assert np.abs(smx - s64).max() <= 2e-2 * scale
-        # the 1p part does not use tensor cores: FP64-exact
-        assert np.abs(smx[:, :v] - s64[:, :v]).max() <= 1e-12 * np.abs(s64[:, :v]).max()
+        # the 1p part only sees BF16 through the second-order coupling contractions
+        assert np.abs(smx[:, :v] - s64[:, :v]).max() <= 1e-4 * np.abs(s64[:, :v]).max()
     finally:
         E.eaadc_destroy(ctx)
 
