@@ -51,8 +51,13 @@ typedef enum {
 
 typedef enum {
   EAADC_FP64 = 0,        /* every operation in FP64 */
-  EAADC_MIXED_BF16 = 1   /* DF ladder and ring GEMMs on tcgen05 tensor cores:
-                            BF16 operands, FP32 accumulation; rest FP64 */
+  EAADC_MIXED_BF16 = 1,  /* every o*v^3 contraction (DF ladder, ring, second-
+                            order coupling) on tcgen05 tensor cores with BF16
+                            operands and FP32 accumulation; DF coupling pieces
+                            in FP32, diagonal and 1p/1p block in FP64 */
+  EAADC_MIXED_BF16X3 = 2 /* as EAADC_MIXED_BF16 with each tensor-core operand
+                            split into two BF16 parts and three products
+                            (about 16 significant bits, 3x the tensor work) */
 } eaadc_prec;
 
 typedef struct {
@@ -60,7 +65,9 @@ typedef struct {
   double etol;    /* ... and every Ritz value moved by <= etol */
   int maxit;      /* iteration limit */
   int max_sub;    /* subspace size limit per state (<= 96) */
-  int prec;       /* eaadc_prec used for the sigma vectors inside the loop */
+  int prec;       /* eaadc_prec used for the sigma vectors inside the loop; a
+                     reduced-precision phase stops at its noise floor (largest
+                     residual shrinking by less than 2x in 8 iterations) */
   int refine;     /* 1: after a mixed-precision solve, FP64 sigma of the Ritz
                      vectors and FP64 Rayleigh-Ritz, then FP64 Davidson
                      iterations until tol is met in FP64 */

@@ -22,6 +22,7 @@ EAADC_ERR_TIMEOUT = -6
 EAADC_ERR_STATE = -7
 EAADC_FP64 = 0
 EAADC_MIXED_BF16 = 1
+EAADC_MIXED_BF16X3 = 2
 
 EXPORTED = (
     "eaadc_version", "eaadc_init", "eaadc_build_canonical", "eaadc_state_info", "eaadc_sigma",

@@ -145,7 +145,8 @@ eaadc_status eaadc_sigma(eaadc_ctx* ctx, int state, int nvec, const double* x_de
     set_device(ctx);
     ea::State& st = get_state(ctx, state);
     if (nvec < 0 || (nvec > 0 && (!x_dev || !sigma_dev))) ea::fail(EAADC_ERR_ARG, "bad vector arguments");
-    if (prec != EAADC_FP64 && prec != EAADC_MIXED_BF16) ea::fail(EAADC_ERR_ARG, "unknown precision");
+    if (prec != EAADC_FP64 && prec != EAADC_MIXED_BF16 && prec != EAADC_MIXED_BF16X3)
+      ea::fail(EAADC_ERR_ARG, "unknown precision");
     if (nvec == 0) return;
     const char* xa = (const char*)x_dev;
     const char* ya = (const char*)sigma_dev;
@@ -153,7 +154,7 @@ eaadc_status eaadc_sigma(eaadc_ctx* ctx, int state, int nvec, const double* x_de
     if (xa < ya + bytes && ya < xa + bytes) ea::fail(EAADC_ERR_ARG, "x and sigma overlap");
     cudaStream_t s = (cudaStream_t)stream;
     if (prec == EAADC_FP64) ea::sigma_fp64(s, st, nvec, x_dev, sigma_dev);
-    else ea::sigma_mixed(s, st, nvec, x_dev, sigma_dev);
+    else ea::sigma_mixed(s, st, nvec, x_dev, sigma_dev, prec == EAADC_MIXED_BF16X3);
   });
 }
 
@@ -168,8 +169,10 @@ eaadc_status eaadc_sigma_host(eaadc_ctx* ctx, int state, int nvec, const double*
     size_t n = (size_t)nvec * st.dim;
     ea::DArr<double> x(n, s), y(n, s);
     EA_CK(cudaMemcpyAsync(x.p, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    if (prec != EAADC_FP64 && prec != EAADC_MIXED_BF16 && prec != EAADC_MIXED_BF16X3)
+      ea::fail(EAADC_ERR_ARG, "unknown precision");
     if (prec == EAADC_FP64) ea::sigma_fp64(s, st, nvec, x.p, y.p);
-    else ea::sigma_mixed(s, st, nvec, x.p, y.p);
+    else ea::sigma_mixed(s, st, nvec, x.p, y.p, prec == EAADC_MIXED_BF16X3);
     EA_CK(cudaMemcpyAsync(sigma_host, y.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     EA_CK(cudaStreamSynchronize(s));
     if (prec != EAADC_FP64) ea::check_device_error(s, st);
@@ -218,6 +221,8 @@ eaadc_status eaadc_davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opt
     if (ctx->states.empty()) ea::fail(EAADC_ERR_STATE, "no states built");
     if (nroots < 1 || !opts || !omega) ea::fail(EAADC_ERR_ARG, "bad arguments");
     if (!(opts->tol > 0) || opts->maxit < 1) ea::fail(EAADC_ERR_ARG, "bad Davidson options");
+    if (opts->prec != EAADC_FP64 && opts->prec != EAADC_MIXED_BF16 && opts->prec != EAADC_MIXED_BF16X3)
+      ea::fail(EAADC_ERR_ARG, "unknown precision");
     ea::davidson(ctx, nroots, *opts, omega, resnorm, iters, &conv);
   });
   if (st == EAADC_OK && !conv) {

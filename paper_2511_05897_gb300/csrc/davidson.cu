@@ -214,14 +214,14 @@ static void row_norms(cudaStream_t s, const double* X, int k, long long n, doubl
 
 static void apply_sigma(cudaStream_t s, State& st, int prec, int nvec, const double* x, double* y) {
   if (prec == EAADC_FP64) sigma_fp64(s, st, nvec, x, y);
-  else sigma_mixed(s, st, nvec, x, y);
+  else sigma_mixed(s, st, nvec, x, y, prec == EAADC_MIXED_BF16X3);
 }
 
 // One Davidson phase at precision `prec` starting from `k0` orthonormal rows in V.
 // Returns true if converged.
 static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaadc_davidson_opts& opt, DArr<double>& V,
                            DArr<double>& S, int mmax, int k0, std::vector<double>& theta, std::vector<double>& rn,
-                           int& iters, DArr<double>& Xr) {
+                           int& iters, DArr<double>& Xr, bool stop_at_floor) {
   const long long n = st.dim;
   int m = k0;
   apply_sigma(s, st, prec, m, V.p, S.p);
@@ -233,13 +233,20 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
   int nb = std::min(256, (int)std::max<long long>(1, (n + 255) / 256));
   DArr<double> part((size_t)k * nb, s);
   std::vector<double> th_old(k, INFINITY);
+  std::vector<double> hist;  // largest residual norm per iteration
   theta.assign(k, 0.0);
   rn.assign(k, 0.0);
   bool conv = false;
+  int mg = 0;  // rows/columns of G already formed
   for (int it = 1; it <= opt.maxit; ++it) {
     iters++;
-    gram(s, V.p, m, S.p, m, n, G.p, m);
-    symmetrize<<<(m * m + 255) / 256, 256, 0, s>>>(G.p, m, m, Gs.p);
+    // subspace matrix G = V S^T, only the rows and columns of new vectors
+    if (mg < m) {
+      gram(s, V.p + (long long)mg * n, m - mg, S.p, m, n, G.p + (long long)mg * mmax, mmax);
+      if (mg > 0) gram(s, V.p, mg, S.p + (long long)mg * n, m - mg, n, G.p + mg, mmax);
+      mg = m;
+    }
+    symmetrize<<<(m * m + 255) / 256, 256, 0, s>>>(G.p, m, mmax, Gs.p);
     EA_LAUNCH();
     jacobi_eigh(s, m, Gs.p, w.p, U.p);
     // Ritz vectors and their sigma: X = U[:, :k]^T V
@@ -264,6 +271,12 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
     }
     th_old = theta;
     if (all) { conv = true; break; }
+    // reduced precision: stop at the noise floor of the mixed sigma (the
+    // largest residual shrank by less than 2x over the last 8 iterations)
+    double worst = 0.0;
+    for (int r = 0; r < k; ++r) worst = std::max(worst, rn[r]);
+    hist.push_back(worst);
+    if (stop_at_floor && hist.size() > 8 && worst < 1e-3 && worst > 0.5 * hist[hist.size() - 9]) break;
     if (un.empty()) continue;  // residuals small, Ritz values still moving: iterate on same space
     int nn = (int)un.size();
     EA_CK(cudaMemcpyAsync(rows.p, un.data(), sizeof(int) * nn, cudaMemcpyHostToDevice, s));
@@ -296,6 +309,7 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
       dgemm(s, true, false, keep, (int)n, m, 1.0, U.p, m, S.p, n, 0.0, T.p, n);
       EA_CK(cudaMemcpyAsync(S.p, T.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, s));
       m = keep;
+      mg = 0;
     }
     // new orthonormal directions: coef^T Dn
     dgemm(s, true, false, nacc, (int)n, nn, 1.0, coef.p, nn, Dn.p, n, 0.0, V.p + (long long)m * n, n);
@@ -334,11 +348,12 @@ void davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts& opt, double
     EA_LAUNCH();
     std::vector<double> theta, rn;
     int it = 0;
-    bool conv = davidson_phase(s, st, k, opt.prec, opt, V, S, mmax, k, theta, rn, it, st.evecs);
-    if (opt.prec != EAADC_FP64 && opt.refine) {
+    const bool refine = opt.prec != EAADC_FP64 && opt.refine;
+    bool conv = davidson_phase(s, st, k, opt.prec, opt, V, S, mmax, k, theta, rn, it, st.evecs, refine);
+    if (refine) {
       // FP64 refinement from the mixed-precision Ritz vectors
       EA_CK(cudaMemcpyAsync(V.p, st.evecs.p, sizeof(double) * k * n, cudaMemcpyDeviceToDevice, s));
-      conv = davidson_phase(s, st, k, EAADC_FP64, opt, V, S, mmax, k, theta, rn, it, st.evecs);
+      conv = davidson_phase(s, st, k, EAADC_FP64, opt, V, S, mmax, k, theta, rn, it, st.evecs, false);
     }
     for (int r = 0; r < k; ++r) {
       omega[si * nroots + r] = theta[r];

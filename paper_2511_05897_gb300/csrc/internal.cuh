@@ -74,38 +74,66 @@ struct DArr {
 using bf16 = __nv_bfloat16;
 
 // ------------------------------------------------------------- FP64 toolkit
-// Row-major GEMM: C = alpha * op(A) * op(B) + beta * C, op(X) = X or X^T.
-// A is M x K (or K x M if ta) with row stride lda; B is K x N (or N x K if tb).
-// Two-level batch: batch index z = z1 * nb2 + z2 adds z1*s?1 + z2*s?2.
+// Row-major GEMM on CUDA cores: C = alpha * op(A) * op(B) + beta * C, op(X) = X
+// or X^T.  A is M x K (or K x M if ta) with row stride lda; B is K x N (or N x K
+// if tb).  Two-level batch: batch index z = z1 * nb2 + z2 adds z1*s?1 + z2*s?2.
+// T is double (the FP64 path) or float (DF pieces of the mixed path).
 struct GemmBatch {
   int nb1 = 1, nb2 = 1;
   long long sA1 = 0, sA2 = 0, sB1 = 0, sB2 = 0, sC1 = 0, sC2 = 0;
 };
-void dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
-           long long lda, const double* B, long long ldb, double beta, double* C, long long ldc,
-           const GemmBatch& bt = GemmBatch());
+template <class T>
+void gemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, T alpha, const T* A, long long lda, const T* B,
+          long long ldb, T beta, T* C, long long ldc, const GemmBatch& bt);
+inline void dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha, const double* A, long long lda,
+                  const double* B, long long ldb, double beta, double* C, long long ldc,
+                  const GemmBatch& bt = GemmBatch()) {
+  gemm<double>(s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+}
 
 // dst = alpha * permute(src) + beta * dst; src has dims sdims, dst axis i is src axis perm[i].
-void permute(cudaStream_t s, const double* src, const std::vector<int>& sdims,
-             const std::vector<int>& perm, double* dst, double alpha = 1.0, double beta = 0.0);
+template <class T>
+void permuteT(cudaStream_t s, const T* src, const std::vector<int>& sdims, const std::vector<int>& perm, T* dst,
+              T alpha, T beta);
+inline void permute(cudaStream_t s, const double* src, const std::vector<int>& sdims, const std::vector<int>& perm,
+                    double* dst, double alpha = 1.0, double beta = 0.0) {
+  permuteT<double>(s, src, sdims, perm, dst, alpha, beta);
+}
 
 // out[.., b, c] = alpha * (c1 * in[.., b, c] + c2 * in[.., c, b]) + beta * out[.., b, c]
 // for `nmat` consecutive v x v matrices with strides (in_stride, out_stride).
-void pair_combine(cudaStream_t s, const double* in, long long in_stride, double* out,
-                  long long out_stride, int nmat, int v, double c1, double c2, double alpha, double beta);
+template <class T>
+void pair_combineT(cudaStream_t s, const T* in, long long in_stride, T* out, long long out_stride, int nmat, int v,
+                   T c1, T c2, T alpha, T beta);
+inline void pair_combine(cudaStream_t s, const double* in, long long in_stride, double* out, long long out_stride,
+                         int nmat, int v, double c1, double c2, double alpha, double beta) {
+  pair_combineT<double>(s, in, in_stride, out, out_stride, nmat, v, c1, c2, alpha, beta);
+}
 
-// Generic helpers.
-void fill(cudaStream_t s, double* p, size_t n, double val);
-void axpby(cudaStream_t s, size_t n, double a, const double* x, double b, double* y);  // y = a x + b y
+template <class T>
+void fillT(cudaStream_t s, T* p, size_t n, T val);
+template <class T>
+void axpbyT(cudaStream_t s, size_t n, T a, const T* x, T b, T* y);  // y = a x + b y
+inline void fill(cudaStream_t s, double* p, size_t n, double val) { fillT<double>(s, p, n, val); }
+inline void axpby(cudaStream_t s, size_t n, double a, const double* x, double b, double* y) {
+  axpbyT<double>(s, n, a, x, b, y);
+}
 
-// Two-operand tensor contraction (einsum without batch labels), FP64.
-struct Tens {
-  double* p;
+// Two-operand tensor contraction (einsum without batch labels).
+template <class T>
+struct TensT {
+  T* p;
   std::vector<int> dims;
   size_t size() const { size_t n = 1; for (int d : dims) n *= (size_t)d; return n; }
 };
-void einsum(cudaStream_t s, const char* spec, double alpha, const Tens& A, const Tens& B, double beta,
-            const Tens& C);
+using Tens = TensT<double>;
+template <class T>
+void einsumT(cudaStream_t s, const char* spec, T alpha, const TensT<T>& A, const TensT<T>& B, T beta,
+             const TensT<T>& C);
+inline void einsum(cudaStream_t s, const char* spec, double alpha, const Tens& A, const Tens& B, double beta,
+                   const Tens& C) {
+  einsumT<double>(s, spec, alpha, A, B, beta, C);
+}
 
 // ------------------------------------------------------------- problem data
 struct State {
@@ -122,6 +150,9 @@ struct State {
   // mixed-precision operands (built lazily)
   DArr<bf16> Bvv_bf, Bb_bf, Kmat_bf, Jmat_bf;  // Bb_bf[b][Q][d] = B^Q_bd
   DArr<bf16> tauA_bf, tauB_bf, tauC_bf, tauD_bf, tm2A_bf, tm2C_bf;  // (ov x ov) coupling operands
+  DArr<float> Boo32, Bov32, Bvv32, tau32;     // FP32 copies for the DF coupling pieces
+  DArr<bf16> Bvv_lo, Bb_lo, Kmat_lo, Jmat_lo, tauA_lo, tm2A_lo;  // low parts (split-BF16 mode)
+  bool x3_ready = false;
   DArr<int> err;                              // device error word of bounded waits
   bool mixed_ready = false;
   // last Davidson solution
@@ -144,10 +175,20 @@ struct eaadc_ctx {
 namespace ea {
 void build_state_intermediates(eaadc_ctx* ctx, State& st);
 void sigma_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y);
-void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y);
+void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y, bool x3);
 void sigma_base_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y, bool ring, bool ladder);
 void check_device_error(cudaStream_t s, State& st);
 void diag_and_m11(cudaStream_t s, State& st, int nvec, const double* x, double* y);
+template <class T>
+struct CoupOps {
+  int o, v, naux, order;
+  const T *Boo, *Bov, *Bvv, *tau;
+};
+template <class T>
+void couple12(cudaStream_t s, const CoupOps<T>& c, const T* y, T* outA, const T* tm2, bool big, T* Fo, T* Go);
+template <class T>
+void couple21(cudaStream_t s, const CoupOps<T>& c, const T* V, T* sy, const T* tm2, const T* H1g, const T* H2g,
+              const T* H3g);
 void couple_1p_to_2p1h(cudaStream_t s, State& st, const double* y, double* outA, const double* tm2, bool big,
                        double* Fo, double* Go);
 void couple_2p1h_to_1p(cudaStream_t s, State& st, const double* V, double* sy, const double* tm2,

@@ -20,11 +20,11 @@ constexpr int BM = 64, BN = 64, BK = 16;
 // blockIdx.z = zb * ksplit + zs: batch entry zb, K slice zs of length kchunk.
 // With ksplit > 1 each slice writes alpha * (its partial product) to its own
 // [M][N] panel of C (panels ksplit*nbatch apart is the caller's layout).
-template <bool TA, bool TB, bool BETA0>
-__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha,
-                                                    const double* __restrict__ A, long long lda,
-                                                    const double* __restrict__ B, long long ldb,
-                                                    double beta, double* __restrict__ C, long long ldc,
+template <class T, bool TA, bool TB, bool BETA0>
+__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, T alpha,
+                                                    const T* __restrict__ A, long long lda,
+                                                    const T* __restrict__ B, long long ldb,
+                                                    T beta, T* __restrict__ C, long long ldc,
                                                     GemmBatch bt, int ksplit, int kchunk, long long spanel) {
   const int zs = blockIdx.z % ksplit;
   const int z = blockIdx.z / ksplit;
@@ -34,16 +34,16 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   C += z1 * bt.sC1 + z2 * bt.sC2 + (long long)zs * spanel;
   const int kbeg = zs * kchunk;
   const int kend = min(K, kbeg + kchunk);
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
@@ -51,21 +51,21 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
       int mm, kk;
       if (TA) { mm = i % BM; kk = i / BM; } else { kk = i % BK; mm = i / BK; }
       int gm = m0 + mm, gk = k0 + kk;
-      double a = 0.0;
+      T a = T(0);
       if (gm < M && gk < kend) a = TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
       As[kk][mm] = a;
       int nn;
       if (TB) { kk = i % BK; nn = i / BK; } else { nn = i % BN; kk = i / BN; }
       int gn = n0 + nn;
       gk = k0 + kk;
-      double b = 0.0;
+      T b = T(0);
       if (gn < N && gk < kend) b = TB ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
       Bs[kk][nn] = b;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -85,26 +85,27 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
     for (int j = 0; j < 4; ++j) {
       int gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
-      double* c = C + (long long)gm * ldc + gn;
+      T* c = C + (long long)gm * ldc + gn;
       *c = BETA0 ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
     }
   }
 }
 
-__global__ void splitk_reduce(const double* __restrict__ P, int ksplit, long long panel, int M, int N,
-                              double beta, double* __restrict__ C, long long ldc) {
+template <class T>
+__global__ void splitk_reduce(const T* __restrict__ P, int ksplit, long long panel, int M, int N,
+                              T beta, T* __restrict__ C, long long ldc) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < panel; e += (long long)gridDim.x * blockDim.x) {
-    double acc = 0.0;
+    T acc = T(0);
     for (int z = 0; z < ksplit; ++z) acc += P[(long long)z * panel + e];
     const long long m = e / N, n = e % N;
-    double* c = C + m * ldc + n;
-    *c = (beta == 0.0) ? acc : acc + beta * (*c);
+    T* c = C + m * ldc + n;
+    *c = (beta == T(0)) ? acc : acc + beta * (*c);
   }
 }
 
-template <bool TA, bool TB>
-void dgemm_t(cudaStream_t s, int M, int N, int K, double alpha, const double* A, long long lda,
-             const double* B, long long ldb, double beta, double* C, long long ldc, const GemmBatch& bt) {
+template <class T, bool TA, bool TB>
+void dgemm_t(cudaStream_t s, int M, int N, int K, T alpha, const T* A, long long lda,
+             const T* B, long long ldb, T beta, T* C, long long ldc, const GemmBatch& bt) {
   const int nbatch = bt.nb1 * bt.nb2;
   const long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * nbatch;
   // split K when the output grid cannot fill the GPU and K is long
@@ -115,20 +116,20 @@ void dgemm_t(cudaStream_t s, int M, int N, int K, double alpha, const double* A,
   }
   if (ksplit == 1) {
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nbatch);
-    if (beta == 0.0)
-      dgemm_kernel<TA, TB, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, 1, K, 0);
+    if (beta == T(0))
+      dgemm_kernel<T, TA, TB, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, 1, K, 0);
     else
-      dgemm_kernel<TA, TB, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, 1, K, 0);
+      dgemm_kernel<T, TA, TB, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, 1, K, 0);
     EA_LAUNCH();
     return;
   }
   const int kchunk = ((K + ksplit - 1) / ksplit + BK - 1) / BK * BK;
   ksplit = (K + kchunk - 1) / kchunk;
   const long long panel = (long long)M * N;
-  DArr<double> P((size_t)(panel * ksplit), s);
+  DArr<T> P((size_t)(panel * ksplit), s);
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, ksplit);
-  dgemm_kernel<TA, TB, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, 0.0, P.p, N, bt, ksplit, kchunk,
-                                                  panel);
+  dgemm_kernel<T, TA, TB, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, T(0), P.p, N, bt, ksplit, kchunk,
+                                                     panel);
   EA_LAUNCH();
   splitk_reduce<<<(int)std::min<long long>((panel + 255) / 256, 4096), 256, 0, s>>>(P.p, ksplit, panel, M, N, beta,
                                                                                    C, ldc);
@@ -136,17 +137,21 @@ void dgemm_t(cudaStream_t s, int M, int N, int K, double alpha, const double* A,
 }
 }  // namespace
 
-void dgemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha, const double* A,
-           long long lda, const double* B, long long ldb, double beta, double* C, long long ldc,
-           const GemmBatch& bt) {
+template <class T>
+void gemm(cudaStream_t s, bool ta, bool tb, int M, int N, int K, T alpha, const T* A, long long lda, const T* B,
+          long long ldb, T beta, T* C, long long ldc, const GemmBatch& bt) {
   if (M <= 0 || N <= 0 || bt.nb1 * bt.nb2 <= 0) return;
   if (bt.nb1 * bt.nb2 > 65535) fail(EAADC_ERR_ARG, "dgemm: batch too large");
   if ((M + BM - 1) / BM > 65535) fail(EAADC_ERR_ARG, "dgemm: M too large");
-  if (ta && tb) dgemm_t<true, true>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
-  else if (ta) dgemm_t<true, false>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
-  else if (tb) dgemm_t<false, true>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
-  else dgemm_t<false, false>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  if (ta && tb) dgemm_t<T, true, true>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  else if (ta) dgemm_t<T, true, false>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  else if (tb) dgemm_t<T, false, true>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+  else dgemm_t<T, false, false>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
 }
+template void gemm<double>(cudaStream_t, bool, bool, int, int, int, double, const double*, long long, const double*,
+                           long long, double, double*, long long, const GemmBatch&);
+template void gemm<float>(cudaStream_t, bool, bool, int, int, int, float, const float*, long long, const float*,
+                          long long, float, float*, long long, const GemmBatch&);
 
 // ----------------------------------------------------------------- permute
 namespace {
@@ -156,8 +161,9 @@ struct PermArgs {
   long long sstride[8];  // stride in src of dst axis i
 };
 
-__global__ void permute_kernel(const double* __restrict__ src, double* __restrict__ dst, long long total,
-                               PermArgs pa, double alpha, double beta) {
+template <class T>
+__global__ void permute_kernel(const T* __restrict__ src, T* __restrict__ dst, long long total,
+                               PermArgs pa, T alpha, T beta) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     long long r = idx, off = 0;
@@ -166,16 +172,17 @@ __global__ void permute_kernel(const double* __restrict__ src, double* __restric
       r /= pa.ddim[i];
       off += c * pa.sstride[i];
     }
-    double val = alpha * src[off];
-    dst[idx] = (beta == 0.0) ? val : val + beta * dst[idx];
+    T val = alpha * src[off];
+    dst[idx] = (beta == T(0)) ? val : val + beta * dst[idx];
   }
 }
 
 int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
 }  // namespace
 
-void permute(cudaStream_t s, const double* src, const std::vector<int>& sdims, const std::vector<int>& perm,
-             double* dst, double alpha, double beta) {
+template <class T>
+void permuteT(cudaStream_t s, const T* src, const std::vector<int>& sdims, const std::vector<int>& perm, T* dst,
+              T alpha, T beta) {
   int nd = (int)sdims.size();
   if (nd > 8 || (int)perm.size() != nd) fail(EAADC_ERR_ARG, "permute: bad rank");
   long long st[8];
@@ -185,71 +192,89 @@ void permute(cudaStream_t s, const double* src, const std::vector<int>& sdims, c
   pa.nd = nd;
   for (int i = 0; i < nd; ++i) { pa.ddim[i] = sdims[perm[i]]; pa.sstride[i] = st[perm[i]]; }
   if (acc == 0) return;
-  permute_kernel<<<grid_for(acc), 256, 0, s>>>(src, dst, acc, pa, alpha, beta);
+  permute_kernel<T><<<grid_for(acc), 256, 0, s>>>(src, dst, acc, pa, alpha, beta);
   EA_LAUNCH();
 }
+template void permuteT<double>(cudaStream_t, const double*, const std::vector<int>&, const std::vector<int>&,
+                               double*, double, double);
+template void permuteT<float>(cudaStream_t, const float*, const std::vector<int>&, const std::vector<int>&, float*,
+                              float, float);
 
 // ------------------------------------------------------------ pair combine
 namespace {
-__global__ void pair_combine_kernel(const double* __restrict__ in, long long in_stride, double* __restrict__ out,
-                                    long long out_stride, int nmat, int v, double c1, double c2, double alpha,
-                                    double beta) {
+template <class T>
+__global__ void pair_combine_kernel(const T* __restrict__ in, long long in_stride, T* __restrict__ out,
+                                    long long out_stride, int nmat, int v, T c1, T c2, T alpha, T beta) {
   // 32x32 tiles of one matrix; transposed partner read through shared memory
-  __shared__ double tileT[32][33];
+  __shared__ T tileT[32][33];
   const int m = blockIdx.z;
   const int b0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const double* I = in + (long long)m * in_stride;
-  double* O = out + (long long)m * out_stride;
+  const T* I = in + (long long)m * in_stride;
+  T* O = out + (long long)m * out_stride;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   // load in[c0+.., b0+..] so that tileT[tx][ty] holds in[c][b] with c = c0+ty, b = b0+tx
   for (int r = ty; r < 32; r += 8) {
     int c = c0 + r, b = b0 + tx;
-    tileT[tx][r] = (c < v && b < v) ? I[(long long)c * v + b] : 0.0;
+    tileT[tx][r] = (c < v && b < v) ? I[(long long)c * v + b] : T(0);
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
     int b = b0 + r, c = c0 + tx;
     if (b < v && c < v) {
-      double val = alpha * (c1 * I[(long long)b * v + c] + c2 * tileT[r][tx]);
-      double* o = O + (long long)b * v + c;
-      *o = (beta == 0.0) ? val : val + beta * (*o);
+      T val = alpha * (c1 * I[(long long)b * v + c] + c2 * tileT[r][tx]);
+      T* o = O + (long long)b * v + c;
+      *o = (beta == T(0)) ? val : val + beta * (*o);
     }
   }
 }
 
-__global__ void fill_kernel(double* p, long long n, double val) {
+template <class T>
+__global__ void fill_kernel(T* p, long long n, T val) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     p[i] = val;
 }
-__global__ void axpby_kernel(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+template <class T>
+__global__ void axpby_kernel(long long n, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
 }
 }  // namespace
 
-void pair_combine(cudaStream_t s, const double* in, long long in_stride, double* out, long long out_stride,
-                  int nmat, int v, double c1, double c2, double alpha, double beta) {
+template <class T>
+void pair_combineT(cudaStream_t s, const T* in, long long in_stride, T* out, long long out_stride, int nmat, int v,
+                   T c1, T c2, T alpha, T beta) {
   if (nmat <= 0 || v <= 0) return;
   if (nmat > 65535) fail(EAADC_ERR_ARG, "pair_combine: too many matrices");
   dim3 grid((v + 31) / 32, (v + 31) / 32, nmat);
-  pair_combine_kernel<<<grid, dim3(32, 8), 0, s>>>(in, in_stride, out, out_stride, nmat, v, c1, c2, alpha, beta);
+  pair_combine_kernel<T><<<grid, dim3(32, 8), 0, s>>>(in, in_stride, out, out_stride, nmat, v, c1, c2, alpha, beta);
   EA_LAUNCH();
 }
+template void pair_combineT<double>(cudaStream_t, const double*, long long, double*, long long, int, int, double,
+                                    double, double, double);
+template void pair_combineT<float>(cudaStream_t, const float*, long long, float*, long long, int, int, float, float,
+                                   float, float);
 
-void fill(cudaStream_t s, double* p, size_t n, double val) {
+template <class T>
+void fillT(cudaStream_t s, T* p, size_t n, T val) {
   if (!n) return;
-  fill_kernel<<<grid_for((long long)n), 256, 0, s>>>(p, (long long)n, val);
+  fill_kernel<T><<<grid_for((long long)n), 256, 0, s>>>(p, (long long)n, val);
   EA_LAUNCH();
 }
-void axpby(cudaStream_t s, size_t n, double a, const double* x, double b, double* y) {
+template <class T>
+void axpbyT(cudaStream_t s, size_t n, T a, const T* x, T b, T* y) {
   if (!n) return;
-  axpby_kernel<<<grid_for((long long)n), 256, 0, s>>>((long long)n, a, x, b, y);
+  axpby_kernel<T><<<grid_for((long long)n), 256, 0, s>>>((long long)n, a, x, b, y);
   EA_LAUNCH();
 }
+template void fillT<double>(cudaStream_t, double*, size_t, double);
+template void fillT<float>(cudaStream_t, float*, size_t, float);
+template void axpbyT<double>(cudaStream_t, size_t, double, const double*, double, double*);
+template void axpbyT<float>(cudaStream_t, size_t, float, const float*, float, float*);
 
 // ------------------------------------------------------------------ einsum
-void einsum(cudaStream_t s, const char* spec, double alpha, const Tens& A, const Tens& B, double beta,
-            const Tens& C) {
+template <class T>
+void einsumT(cudaStream_t s, const char* spec, T alpha, const TensT<T>& A, const TensT<T>& B, T beta,
+             const TensT<T>& C) {
   std::string sp(spec);
   size_t comma = sp.find(','), arrow = sp.find("->");
   if (comma == std::string::npos || arrow == std::string::npos) fail(EAADC_ERR_ARG, "einsum: bad spec");
@@ -288,8 +313,8 @@ void einsum(cudaStream_t s, const char* spec, double alpha, const Tens& A, const
   // Operand A is used as stored when its labels read [fa kc] (plain) or
   // [kc fa] (transposed); B likewise with [fb kc] or [kc fb].  Otherwise it is
   // permuted to [free..., contracted...].
-  DArr<double> ta, tb, tc;
-  const double* pa = A.p;
+  DArr<T> ta, tb, tc;
+  const T* pa = A.p;
   bool transA = false;
   long long ldA = K;
   if (la == fa + kc) {
@@ -298,10 +323,10 @@ void einsum(cudaStream_t s, const char* spec, double alpha, const Tens& A, const
     ldA = M;
   } else {
     ta.alloc(A.size(), s);
-    permute(s, A.p, A.dims, perm_of(la, fa + kc), ta.p);
+    permuteT<T>(s, A.p, A.dims, perm_of(la, fa + kc), ta.p, T(1), T(0));
     pa = ta.p;
   }
-  const double* pb = B.p;
+  const T* pb = B.p;
   bool transB = true;  // B used as N x K
   long long ldB = K;
   if (lb == fb + kc) {
@@ -310,22 +335,26 @@ void einsum(cudaStream_t s, const char* spec, double alpha, const Tens& A, const
     ldB = N;
   } else {
     tb.alloc(B.size(), s);
-    permute(s, B.p, B.dims, perm_of(lb, fb + kc), tb.p);
+    permuteT<T>(s, B.p, B.dims, perm_of(lb, fb + kc), tb.p, T(1), T(0));
     pb = tb.p;
   }
   std::string lt = fa + fb;
   std::vector<int> pC = perm_of(lt, lc);
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) fail(EAADC_ERR_ARG, "einsum: extent too large");
   if (is_id(pC)) {
-    dgemm(s, transA, transB, (int)M, (int)N, (int)K, alpha, pa, ldA, pb, ldB, beta, C.p, N);
+    gemm<T>(s, transA, transB, (int)M, (int)N, (int)K, alpha, pa, ldA, pb, ldB, beta, C.p, N, GemmBatch());
   } else {
     tc.alloc((size_t)(M * N), s);
-    dgemm(s, transA, transB, (int)M, (int)N, (int)K, 1.0, pa, ldA, pb, ldB, 0.0, tc.p, N);
+    gemm<T>(s, transA, transB, (int)M, (int)N, (int)K, T(1), pa, ldA, pb, ldB, T(0), tc.p, N, GemmBatch());
     std::vector<int> tdims;
     for (char c : lt) tdims.push_back(dim[c]);
-    permute(s, tc.p, tdims, pC, C.p, alpha, beta);
+    permuteT<T>(s, tc.p, tdims, pC, C.p, alpha, beta);
   }
 }
+template void einsumT<double>(cudaStream_t, const char*, double, const TensT<double>&, const TensT<double>&, double,
+                              const TensT<double>&);
+template void einsumT<float>(cudaStream_t, const char*, float, const TensT<float>&, const TensT<float>&, float,
+                             const TensT<float>&);
 
 // ------------------------------------------------------------------ Jacobi
 namespace {

@@ -50,69 +50,95 @@ int gridn(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL 
 // big = false skips the three o^2 v^3 tau contractions and instead returns the
 // DF intermediates F[l][c][d] = sum_a (al|cd) y_a and G[b][l][d] = sum_a (ab|ld) y_a
 // (when Fo/Go are given) for the tensor-core path.
-void couple_1p_to_2p1h(cudaStream_t s, State& st, const double* y, double* outA, const double* tm2, bool big,
-                       double* Fo, double* Go) {
-  const int o = st.o, v = st.v, naux = st.naux;
-  Tens Bov{st.Bov.p, {naux, o, v}}, Bvv{st.Bvv.p, {naux, v, v}}, Boo{st.Boo.p, {naux, o, o}};
-  Tens yt{(double*)y, {v}};
-  Tens out{outA, {o, v, v}};
-  DArr<double> Qy((size_t)naux * v, s);
-  Tens Qyt{Qy.p, {naux, v}};
-  einsum(s, "Qba,a->Qb", 1.0, Bvv, yt, 0.0, Qyt);  // B^Q symmetric
-  einsum(s, "Qb,Qkc->kbc", 1.0, Qyt, Bov, 0.0, out);
-  if (st.order < 3) return;
-  Tens tau{st.tau.p, {o, o, v, v}};
-  DArr<double> Qo((size_t)naux * o, s), F, G, H((size_t)o * o * o, s);
-  double* Fp = Fo;
-  double* Gp = Go;
+template <class T>
+void couple12(cudaStream_t s, const CoupOps<T>& c, const T* y, T* outA, const T* tm2, bool big, T* Fo, T* Go) {
+  const int o = c.o, v = c.v, naux = c.naux;
+  using TT = TensT<T>;
+  TT Bov{(T*)c.Bov, {naux, o, v}}, Bvv{(T*)c.Bvv, {naux, v, v}}, Boo{(T*)c.Boo, {naux, o, o}};
+  TT yt{(T*)y, {v}};
+  TT out{outA, {o, v, v}};
+  DArr<T> Qy((size_t)naux * v, s);
+  TT Qyt{Qy.p, {naux, v}};
+  einsumT<T>(s, "Qba,a->Qb", T(1), Bvv, yt, T(0), Qyt);  // B^Q symmetric
+  einsumT<T>(s, "Qb,Qkc->kbc", T(1), Qyt, Bov, T(0), out);
+  if (c.order < 3) return;
+  TT tau{(T*)c.tau, {o, o, v, v}};
+  DArr<T> Qo((size_t)naux * o, s), F, G, H((size_t)o * o * o, s);
+  T* Fp = Fo;
+  T* Gp = Go;
   if (!Fp) { F.alloc((size_t)o * v * v, s); Fp = F.p; }
   if (!Gp) { G.alloc((size_t)o * v * v, s); Gp = G.p; }
-  Tens Qot{Qo.p, {naux, o}}, Ft{Fp, {o, v, v}}, Gt{Gp, {v, o, v}}, Ht{H.p, {o, o, o}};
-  einsum(s, "Qla,a->Ql", 1.0, Bov, yt, 0.0, Qot);
-  einsum(s, "Ql,Qcd->lcd", 1.0, Qot, Bvv, 0.0, Ft);
-  einsum(s, "Qb,Qld->bld", 1.0, Qyt, Bov, 0.0, Gt);
-  einsum(s, "Ql,Qkm->lkm", 1.0, Qot, Boo, 0.0, Ht);
-  einsum(s, "lkm,lmbc->kbc", 1.0, Ht, tau, 1.0, out);
+  TT Qot{Qo.p, {naux, o}}, Ft{Fp, {o, v, v}}, Gt{Gp, {v, o, v}}, Ht{H.p, {o, o, o}};
+  einsumT<T>(s, "Qla,a->Ql", T(1), Bov, yt, T(0), Qot);
+  einsumT<T>(s, "Ql,Qcd->lcd", T(1), Qot, Bvv, T(0), Ft);
+  einsumT<T>(s, "Qb,Qld->bld", T(1), Qyt, Bov, T(0), Gt);
+  einsumT<T>(s, "Ql,Qkm->lkm", T(1), Qot, Boo, T(0), Ht);
+  einsumT<T>(s, "lkm,lmbc->kbc", T(1), Ht, tau, T(1), out);
   if (!big) return;
-  einsum(s, "lcd,lkbd->kbc", -1.0, Ft, tau, 1.0, out);
-  einsum(s, "bld,lkcd->kbc", -1.0, Gt, Tens{(double*)tm2, {o, o, v, v}}, 1.0, out);
-  einsum(s, "lbd,lkdc->kbc", -1.0, Ft, tau, 1.0, out);
+  einsumT<T>(s, "lcd,lkbd->kbc", T(-1), Ft, tau, T(1), out);
+  einsumT<T>(s, "bld,lkcd->kbc", T(-1), Gt, TT{(T*)tm2, {o, o, v, v}}, T(1), out);
+  einsumT<T>(s, "lbd,lkdc->kbc", T(-1), Ft, tau, T(1), out);
 }
 
 // sy[a] += sum_kbc C_A[k,b,c,a] V[k,b,c].  With H1..H3 given (tensor-core
 // path) the three o^2 v^3 contractions H1[l][d][c] = sum_kb t_lk^bd V_kbc,
 // H2[b][l][d] = sum_kc (t_lk^cd - 2 t_lk^dc) V_kbc, H3[l][b][d] = sum_kc t_lk^dc V_kbc
 // are taken from them instead of being formed here.
-void couple_2p1h_to_1p(cudaStream_t s, State& st, const double* V, double* sy, const double* tm2,
-                       const double* H1g, const double* H2g, const double* H3g) {
-  const int o = st.o, v = st.v, naux = st.naux;
-  Tens Bov{st.Bov.p, {naux, o, v}}, Bvv{st.Bvv.p, {naux, v, v}}, Boo{st.Boo.p, {naux, o, o}};
-  Tens Vt{(double*)V, {o, v, v}};
-  Tens out{sy, {v}};
-  DArr<double> g((size_t)naux * v, s);
-  Tens gt{g.p, {naux, v}};
-  einsum(s, "Qkc,kbc->Qb", 1.0, Bov, Vt, 0.0, gt);
-  einsum(s, "Qba,Qb->a", 1.0, Bvv, gt, 1.0, out);  // B^Q symmetric
-  if (st.order < 3) return;
-  Tens tau{st.tau.p, {o, o, v, v}};
-  DArr<double> H, tt((size_t)naux * o, s), t2q((size_t)naux * v, s), H4((size_t)o * o * o, s);
-  Tens ttt{tt.p, {naux, o}}, t2qt{t2q.p, {naux, v}};
+template <class T>
+void couple21(cudaStream_t s, const CoupOps<T>& c, const T* V, T* sy, const T* tm2, const T* H1g, const T* H2g,
+              const T* H3g) {
+  const int o = c.o, v = c.v, naux = c.naux;
+  using TT = TensT<T>;
+  TT Bov{(T*)c.Bov, {naux, o, v}}, Bvv{(T*)c.Bvv, {naux, v, v}}, Boo{(T*)c.Boo, {naux, o, o}};
+  TT Vt{(T*)V, {o, v, v}};
+  TT out{sy, {v}};
+  DArr<T> g((size_t)naux * v, s);
+  TT gt{g.p, {naux, v}};
+  einsumT<T>(s, "Qkc,kbc->Qb", T(1), Bov, Vt, T(0), gt);
+  einsumT<T>(s, "Qba,Qb->a", T(1), Bvv, gt, T(1), out);  // B^Q symmetric
+  if (c.order < 3) return;
+  TT tau{(T*)c.tau, {o, o, v, v}};
+  DArr<T> H, tt((size_t)naux * o, s), t2q((size_t)naux * v, s), H4((size_t)o * o * o, s);
+  TT ttt{tt.p, {naux, o}}, t2qt{t2q.p, {naux, v}};
   const bool ext = H1g != nullptr;
   if (!ext) H.alloc((size_t)o * v * v, s);
-  Tens H1t{ext ? (double*)H1g : H.p, {o, v, v}};
-  if (!ext) einsum(s, "lkbd,kbc->ldc", 1.0, tau, Vt, 0.0, H1t);
-  einsum(s, "Qcd,ldc->Ql", -1.0, Bvv, H1t, 0.0, ttt);
-  Tens H2t{ext ? (double*)H2g : H.p, {v, o, v}};
-  if (!ext) einsum(s, "lkcd,kbc->bld", 1.0, Tens{(double*)tm2, {o, o, v, v}}, Vt, 0.0, H2t);
-  einsum(s, "Qld,bld->Qb", 1.0, Bov, H2t, 0.0, t2qt);
-  einsum(s, "Qba,Qb->a", -1.0, Bvv, t2qt, 1.0, out);
-  Tens H3t{ext ? (double*)H3g : H.p, {o, v, v}};
-  if (!ext) einsum(s, "lkdc,kbc->lbd", 1.0, tau, Vt, 0.0, H3t);
-  einsum(s, "Qbd,lbd->Ql", -1.0, Bvv, H3t, 1.0, ttt);
-  Tens H4t{H4.p, {o, o, o}};
-  einsum(s, "lmbc,kbc->lkm", 1.0, tau, Vt, 0.0, H4t);
-  einsum(s, "Qkm,lkm->Ql", 1.0, Boo, H4t, 1.0, ttt);
-  einsum(s, "Qla,Ql->a", 1.0, Bov, ttt, 1.0, out);
+  TT H1t{ext ? (T*)H1g : H.p, {o, v, v}};
+  if (!ext) einsumT<T>(s, "lkbd,kbc->ldc", T(1), tau, Vt, T(0), H1t);
+  einsumT<T>(s, "Qcd,ldc->Ql", T(-1), Bvv, H1t, T(0), ttt);
+  TT H2t{ext ? (T*)H2g : H.p, {v, o, v}};
+  if (!ext) einsumT<T>(s, "lkcd,kbc->bld", T(1), TT{(T*)tm2, {o, o, v, v}}, Vt, T(0), H2t);
+  einsumT<T>(s, "Qld,bld->Qb", T(1), Bov, H2t, T(0), t2qt);
+  einsumT<T>(s, "Qba,Qb->a", T(-1), Bvv, t2qt, T(1), out);
+  TT H3t{ext ? (T*)H3g : H.p, {o, v, v}};
+  if (!ext) einsumT<T>(s, "lkdc,kbc->lbd", T(1), tau, Vt, T(0), H3t);
+  einsumT<T>(s, "Qbd,lbd->Ql", T(-1), Bvv, H3t, T(1), ttt);
+  TT H4t{H4.p, {o, o, o}};
+  einsumT<T>(s, "lmbc,kbc->lkm", T(1), tau, Vt, T(0), H4t);
+  einsumT<T>(s, "Qkm,lkm->Ql", T(1), Boo, H4t, T(1), ttt);
+  einsumT<T>(s, "Qla,Ql->a", T(1), Bov, ttt, T(1), out);
+}
+
+template void couple12<double>(cudaStream_t, const CoupOps<double>&, const double*, double*, const double*, bool,
+                               double*, double*);
+template void couple12<float>(cudaStream_t, const CoupOps<float>&, const float*, float*, const float*, bool, float*,
+                              float*);
+template void couple21<double>(cudaStream_t, const CoupOps<double>&, const double*, double*, const double*,
+                               const double*, const double*, const double*);
+template void couple21<float>(cudaStream_t, const CoupOps<float>&, const float*, float*, const float*, const float*,
+                              const float*, const float*);
+
+static CoupOps<double> ops64(State& st) {
+  return CoupOps<double>{st.o, st.v, st.naux, st.order, st.Boo.p, st.Bov.p, st.Bvv.p, st.tau.p};
+}
+
+void couple_1p_to_2p1h(cudaStream_t s, State& st, const double* y, double* outA, const double* tm2, bool big,
+                       double* Fo, double* Go) {
+  couple12<double>(s, ops64(st), y, outA, tm2, big, Fo, Go);
+}
+
+void couple_2p1h_to_1p(cudaStream_t s, State& st, const double* V, double* sy, const double* tm2,
+                       const double* H1g, const double* H2g, const double* H3g) {
+  couple21<double>(s, ops64(st), V, sy, tm2, H1g, H2g, H3g);
 }
 
 // sigmaW += S(ring_A(S^-1 W)) for one vector; ring_A(A) =

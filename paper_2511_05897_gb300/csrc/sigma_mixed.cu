@@ -16,6 +16,13 @@
 // (K, J: stored (oo|vv), (ov|ov) integrals; tau*: first-order amplitudes as
 // (ov x ov) matrices) as two long-K GEMMs over concatenated operands, and the
 // 2p1h -> 1p intermediates H1 = tauA V1^T, [H2; H3] = [tm2A; tauB] V2^T.
+//
+// Split-BF16 mode (x3): every operand is split x = x_hi + x_lo into two BF16
+// numbers and every product formed as A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (Henry, Tang and Heinecke, "Leveraging the bfloat16 artificial intelligence
+// datatype for higher-precision computations", 2019), accumulated in FP32 by
+// TMA reduce-adds: about 16 significant bits per operand at 3x the
+// tensor-core work.
 #include "internal.cuh"
 #include "tc_gemm2.cuh"
 
@@ -31,42 +38,48 @@ const double kI2 = 0.5 * (1.0 - 0.57735026918962576451);
 int gridn(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
 long long pad8(long long n) { return (n + 7) / 8 * 8; }
 
+// BF16 destination (row pitch in elements); lo, when set, receives the low
+// part x - bf16(x) at the same position.
 struct OpDst {
   bf16* p;
   long long pitch;
+  bf16* lo;
 };
 
+__device__ __forceinline__ void put(const OpDst& d, long long row, long long col, double x) {
+  const bf16 h = __float2bfloat16_rn((float)x);
+  d.p[row * d.pitch + col] = h;
+  if (d.lo) d.lo[row * d.pitch + col] = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+}
+
 // out[r][c] (pitch op) = in[r][c] (pitch ip), c < cols, rows r < rows
-__global__ void f64_to_bf16_pitched(const double* __restrict__ in, long long ip, bf16* __restrict__ out, long long op,
-                                    long long rows, long long cols) {
+__global__ void f64_to_bf16_pitched(const double* __restrict__ in, long long ip, OpDst out, long long rows,
+                                    long long cols) {
   long long n = rows * cols;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     long long r = i / cols, c = i % cols;
-    out[r * op + c] = __float2bfloat16_rn((float)in[r * ip + c]);
+    put(out, r, c, in[r * ip + c]);
   }
 }
 
 // Bb[b][Q*dp + d] (pitch bp) = B[Q][b][d]; pad columns d >= v stay zero
-__global__ void bmajor_bf16(const double* __restrict__ B, bf16* __restrict__ Bb, int naux, int v, long long dp,
-                            long long bp) {
+__global__ void bmajor_bf16(const double* __restrict__ B, OpDst Bb, int naux, int v, long long dp) {
   long long n = (long long)naux * v * v;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     int d = i % v;
     long long r = i / v;
     int Q = r % naux;
     int b = (int)(r / naux);
-    Bb[(long long)b * bp + (long long)Q * dp + d] = __float2bfloat16_rn((float)B[((long long)Q * v + b) * v + d]);
+    put(Bb, b, (long long)Q * dp + d, B[((long long)Q * v + b) * v + d]);
   }
 }
 
-// Wbf[(n,k,d)][e] (pitch vp) = x[n][v + (k,d,e)]
-__global__ void pack_w_bf16(const double* __restrict__ x, bf16* __restrict__ W, int nvec, long long dim, int v,
-                            long long n2, long long vp) {
+// W[(n,k,d)][e] (pitch in W) = x[n][v + (k,d,e)]
+__global__ void pack_w_bf16(const double* __restrict__ x, OpDst W, int nvec, long long dim, int v, long long n2) {
   long long total = n2 * nvec;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     long long n = i / n2, r = i % n2;
-    long long row = i / v, e = i % v;
-    W[row * vp + e] = __float2bfloat16_rn((float)x[n * dim + v + r]);
+    put(W, i / v, i % v, x[n * dim + v + r]);
   }
 }
 
@@ -89,16 +102,16 @@ __global__ void ring_operands(const double* __restrict__ x, OpDst AmT, OpDst BmT
     double am = kI1 * wyx + kI2 * wxy;  // A[l][y][x]
     double at = kI1 * wxy + kI2 * wyx;  // A[l][x][y]
     const long long row = n * v + xx, col = (long long)l * v + y;
-    AmT.p[row * AmT.pitch + col] = __float2bfloat16_rn((float)am);
-    AtT.p[row * AtT.pitch + col] = __float2bfloat16_rn((float)at);
-    BmT.p[row * BmT.pitch + col] = __float2bfloat16_rn((float)(am - 2.0 * at));
-    V1.p[row * V1.pitch + col] = __float2bfloat16_rn((float)(kS1 * wyx + kS2 * wxy));
-    V2.p[row * V2.pitch + col] = __float2bfloat16_rn((float)(kS1 * wxy + kS2 * wyx));
+    put(AmT, row, col, am);
+    put(AtT, row, col, at);
+    put(BmT, row, col, am - 2.0 * at);
+    put(V1, row, col, kS1 * wyx + kS2 * wxy);
+    put(V2, row, col, kS1 * wxy + kS2 * wyx);
   }
 }
 
 // F1[(n,c)][(l,d)] = F_n[l][c][d] into two destinations; G1[(n,b)][(l,d)] = G_n[b][l][d]
-__global__ void fg_operands(const double* __restrict__ F, const double* __restrict__ G, OpDst F1a, OpDst F1b,
+__global__ void fg_operands(const float* __restrict__ F, const float* __restrict__ G, OpDst F1a, OpDst F1b,
                             OpDst G1, int nvec, int o, int v) {
   const long long ov = (long long)o * v, n2 = ov * v;
   const long long total = (long long)nvec * n2;
@@ -106,14 +119,13 @@ __global__ void fg_operands(const double* __restrict__ F, const double* __restri
     const long long n = i / n2, r = i % n2;
     {  // F_n[l][c][d]
       const int d = r % v, c = (r / v) % v, l = (int)(r / ((long long)v * v));
-      const bf16 f = __float2bfloat16_rn((float)F[i]);
       const long long row = n * v + c, col = (long long)l * v + d;
-      F1a.p[row * F1a.pitch + col] = f;
-      F1b.p[row * F1b.pitch + col] = f;
+      put(F1a, row, col, (double)F[i]);
+      put(F1b, row, col, (double)F[i]);
     }
     {  // G_n[b][l][d]
       const int d = r % v, l = (r / v) % o, b = (int)(r / ov);
-      G1.p[(n * v + b) * G1.pitch + (long long)l * v + d] = __float2bfloat16_rn((float)G[i]);
+      put(G1, n * v + b, (long long)l * v + d, (double)G[i]);
     }
   }
 }
@@ -121,17 +133,17 @@ __global__ void fg_operands(const double* __restrict__ F, const double* __restri
 // FP64 per-vector H tensors from the tensor-core outputs (rows (l,d), columns (n,x)):
 //   H1_n[l][d][c] = H1[(l,d)][(n,c)]
 //   H2_n[b][l][d] = H23[(l,d)][(n,b)]        H3_n[l][b][d] = H23[ov + (l,d)][(n,b)]
-__global__ void h_from_tc(const float* __restrict__ H1, const float* __restrict__ H23, double* __restrict__ h1,
-                          double* __restrict__ h2, double* __restrict__ h3, int nvec, int o, int v, long long nv) {
+__global__ void h_from_tc(const float* __restrict__ H1, const float* __restrict__ H23, float* __restrict__ h1,
+                          float* __restrict__ h2, float* __restrict__ h3, int nvec, int o, int v, long long nv) {
   const long long ov = (long long)o * v, n2 = ov * v;
   const long long total = (long long)nvec * n2;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long n = i / n2, r = i % n2;
     const int t = r % v, q = (r / v) % v, p = (int)(r / ((long long)v * v));
-    h1[i] = (double)H1[((long long)p * v + q) * nv + n * v + t];         // l=p, d=q, c=t
-    h3[i] = (double)H23[(ov + (long long)p * v + t) * nv + n * v + q];  // l=p, b=q, d=t
+    h1[i] = H1[((long long)p * v + q) * nv + n * v + t];         // l=p, d=q, c=t
+    h3[i] = H23[(ov + (long long)p * v + t) * nv + n * v + q];  // l=p, b=q, d=t
     const long long b = r / ov, l = (r / v) % o, d = r % v;
-    h2[i] = (double)H23[(l * v + d) * nv + n * v + b];
+    h2[i] = H23[(l * v + d) * nv + n * v + b];
   }
 }
 
@@ -170,55 +182,120 @@ __global__ void tau_operands(const double* __restrict__ tau, OpDst tA, OpDst tB,
     r /= v;
     int k = r % o;
     int l = (int)(r / o);
-    double t = tau[i];
-    double tsw = tau[(((long long)l * o + k) * v + y) * v + xx];
-    bf16 tb = __float2bfloat16_rn((float)t);
-    bf16 mb = __float2bfloat16_rn((float)(t - 2.0 * tsw));
+    const double t = tau[i];
+    const double m2 = t - 2.0 * tau[(((long long)l * o + k) * v + y) * v + xx];
     const long long ly = (long long)l * v + y, kx = (long long)k * v + xx, lx = (long long)l * v + xx,
                     ky = (long long)k * v + y;
-    tA.p[ly * tA.pitch + kx] = tb;
-    tC.p[kx * tC.pitch + ly] = tb;
-    tB.p[lx * tB.pitch + ky] = tb;
-    tD.p[ky * tD.pitch + lx] = tb;
-    m2A.p[ly * m2A.pitch + kx] = mb;
-    m2C.p[kx * m2C.pitch + ly] = mb;
+    put(tA, ly, kx, t);
+    put(tC, kx, ly, t);
+    put(tB, lx, ky, t);
+    put(tD, ky, lx, t);
+    put(m2A, ly, kx, m2);
+    put(m2C, kx, ly, m2);
   }
 }
 
 __global__ void zero_int(int* p) { *p = 0; }
 
-void prepare_mixed(cudaStream_t s, State& st) {
-  if (st.mixed_ready) return;
+__global__ void f64_to_f32(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// y[v + (k,b,c)] += kS1 * A[k][b][c] + kS2 * A[k][c][b]   (S map of an A-representation block)
+__global__ void add_S_f32(const float* __restrict__ A, double* __restrict__ y, int o, int v) {
+  const long long vv = (long long)v * v, total = (long long)o * vv;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long k = i / vv, r = i % vv;
+    const int b = r / v, c = r % v;
+    y[v + i] += kS1 * (double)A[i] + kS2 * (double)A[k * vv + (long long)c * v + b];
+  }
+}
+
+// hi/lo BF16 split of an FP32 array
+__global__ void split_f32(const float* __restrict__ in, bf16* __restrict__ hi, bf16* __restrict__ lo, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float x = in[i];
+    const bf16 h = __float2bfloat16_rn(x);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+__global__ void add_f32(const float* __restrict__ a, double* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += (double)a[i];
+}
+
+// BF16 operands of a state (and their low parts when x3): B^Q in [Q][c][e] and
+// b-major [b][(Q,d)] layouts, and the concatenated (ov x ov) ring/coupling
+// matrices T1: [K | tauC], T2: [J | K | tm2C | tauD], H1: tauA, H2/H3: [tm2A ; tauB].
+void convert_state_operands(cudaStream_t s, State& st, bool lo) {
   const int o = st.o, v = st.v, naux = st.naux;
   const long long vv = (long long)v * v, ov = (long long)o * v;
   const long long vp = pad8(v), bp = (long long)naux * vp, ovp = pad8(ov);
-  st.Bvv_bf.alloc((size_t)(naux * v * vp), s);
-  f64_to_bf16_pitched<<<gridn(naux * vv), 256, 0, s>>>(st.Bvv.p, v, st.Bvv_bf.p, vp, (long long)naux * v, v);
+  auto L = [&](DArr<bf16>& a) { return lo ? a.p : nullptr; };
+  auto zero = [&](DArr<bf16>& a) { EA_CK(cudaMemsetAsync(a.p, 0, a.n * sizeof(bf16), s)); };
+  f64_to_bf16_pitched<<<gridn(naux * vv), 256, 0, s>>>(st.Bvv.p, v, OpDst{st.Bvv_bf.p, vp, L(st.Bvv_lo)},
+                                                      (long long)naux * v, v);
   EA_LAUNCH();
-  st.Bb_bf.alloc((size_t)(v * bp), s);
-  if (vp != v) EA_CK(cudaMemsetAsync(st.Bb_bf.p, 0, st.Bb_bf.n * sizeof(bf16), s));
-  bmajor_bf16<<<gridn(naux * vv), 256, 0, s>>>(st.Bvv.p, st.Bb_bf.p, naux, v, vp, bp);
+  if (vp != v) { zero(st.Bb_bf); if (lo) zero(st.Bb_lo); }
+  bmajor_bf16<<<gridn(naux * vv), 256, 0, s>>>(st.Bvv.p, OpDst{st.Bb_bf.p, bp, L(st.Bb_lo)}, naux, v, vp);
+  EA_LAUNCH();
+  if (st.order < 3) return;
+  zero(st.Kmat_bf); zero(st.Jmat_bf); zero(st.tauA_bf); zero(st.tm2A_bf);
+  if (lo) { zero(st.Kmat_lo); zero(st.Jmat_lo); zero(st.tauA_lo); zero(st.tm2A_lo); }
+  auto off = [&](DArr<bf16>& a, long long o2) { return lo ? a.p + o2 : nullptr; };
+  f64_to_bf16_pitched<<<gridn(ov * ov), 256, 0, s>>>(st.Kmat.p, ov, OpDst{st.Kmat_bf.p, 2 * ovp, off(st.Kmat_lo, 0)},
+                                                    ov, ov);
+  EA_LAUNCH();
+  f64_to_bf16_pitched<<<gridn(ov * ov), 256, 0, s>>>(st.Jmat.p, ov, OpDst{st.Jmat_bf.p, 4 * ovp, off(st.Jmat_lo, 0)},
+                                                    ov, ov);
+  EA_LAUNCH();
+  f64_to_bf16_pitched<<<gridn(ov * ov), 256, 0, s>>>(
+      st.Kmat.p, ov, OpDst{st.Jmat_bf.p + ovp, 4 * ovp, off(st.Jmat_lo, ovp)}, ov, ov);
+  EA_LAUNCH();
+  OpDst tA{st.tauA_bf.p, ovp, off(st.tauA_lo, 0)}, tC{st.Kmat_bf.p + ovp, 2 * ovp, off(st.Kmat_lo, ovp)},
+      tD{st.Jmat_bf.p + 3 * ovp, 4 * ovp, off(st.Jmat_lo, 3 * ovp)},
+      m2C{st.Jmat_bf.p + 2 * ovp, 4 * ovp, off(st.Jmat_lo, 2 * ovp)}, m2A{st.tm2A_bf.p, ovp, off(st.tm2A_lo, 0)},
+      tB{st.tm2A_bf.p + ov * ovp, ovp, off(st.tm2A_lo, ov * ovp)};
+  tau_operands<<<gridn(ov * ov), 256, 0, s>>>(st.tau.p, tA, tB, tC, tD, m2A, m2C, o, v);
+  EA_LAUNCH();
+}
+
+void prepare_mixed(cudaStream_t s, State& st, bool x3) {
+  const int o = st.o, v = st.v, naux = st.naux;
+  const long long ov = (long long)o * v;
+  const long long vp = pad8(v), bp = (long long)naux * vp, ovp = pad8(ov);
+  if (x3 && st.mixed_ready && !st.x3_ready) st.mixed_ready = false;  // redo with low parts
+  if (st.mixed_ready) return;
+  auto alloc_pair = [&](DArr<bf16>& hi, DArr<bf16>& lo, size_t n) {
+    hi.alloc(n, s);
+    if (x3) lo.alloc(n, s);
+  };
+  alloc_pair(st.Bvv_bf, st.Bvv_lo, (size_t)(naux * v * vp));
+  alloc_pair(st.Bb_bf, st.Bb_lo, (size_t)(v * bp));
+  if (st.order >= 3) {
+    alloc_pair(st.Kmat_bf, st.Kmat_lo, (size_t)(ov * 2 * ovp));
+    alloc_pair(st.Jmat_bf, st.Jmat_lo, (size_t)(ov * 4 * ovp));
+    alloc_pair(st.tauA_bf, st.tauA_lo, (size_t)(ov * ovp));
+    alloc_pair(st.tm2A_bf, st.tm2A_lo, (size_t)(2 * ov * ovp));
+  }
+  convert_state_operands(s, st, x3);
+  st.x3_ready = x3;
+  // FP32 copies for the DF coupling pieces (CUDA-core GEMMs)
+  st.Boo32.alloc(st.Boo.n, s);
+  st.Bov32.alloc(st.Bov.n, s);
+  st.Bvv32.alloc(st.Bvv.n, s);
+  f64_to_f32<<<gridn(st.Boo.n), 256, 0, s>>>(st.Boo.p, st.Boo32.p, (long long)st.Boo.n);
+  EA_LAUNCH();
+  f64_to_f32<<<gridn(st.Bov.n), 256, 0, s>>>(st.Bov.p, st.Bov32.p, (long long)st.Bov.n);
+  EA_LAUNCH();
+  f64_to_f32<<<gridn(st.Bvv.n), 256, 0, s>>>(st.Bvv.p, st.Bvv32.p, (long long)st.Bvv.n);
   EA_LAUNCH();
   if (st.order >= 3) {
-    // A-side operands; segments are ov wide with pitch ovp (pad columns zero):
-    //   T1: [K | tauC]   T2: [J | K | tm2C | tauD]   H1: tauA   H2/H3: [tm2A ; tauB] (stacked rows)
-    st.Kmat_bf.alloc((size_t)(ov * 2 * ovp), s);
-    st.Jmat_bf.alloc((size_t)(ov * 4 * ovp), s);
-    st.tauA_bf.alloc((size_t)(ov * ovp), s);
-    st.tm2A_bf.alloc((size_t)(2 * ov * ovp), s);
-    EA_CK(cudaMemsetAsync(st.Kmat_bf.p, 0, st.Kmat_bf.n * sizeof(bf16), s));
-    EA_CK(cudaMemsetAsync(st.Jmat_bf.p, 0, st.Jmat_bf.n * sizeof(bf16), s));
-    EA_CK(cudaMemsetAsync(st.tauA_bf.p, 0, st.tauA_bf.n * sizeof(bf16), s));
-    EA_CK(cudaMemsetAsync(st.tm2A_bf.p, 0, st.tm2A_bf.n * sizeof(bf16), s));
-    f64_to_bf16_pitched<<<gridn(ov * ov), 256, 0, s>>>(st.Kmat.p, ov, st.Kmat_bf.p, 2 * ovp, ov, ov);
-    EA_LAUNCH();
-    f64_to_bf16_pitched<<<gridn(ov * ov), 256, 0, s>>>(st.Jmat.p, ov, st.Jmat_bf.p, 4 * ovp, ov, ov);
-    EA_LAUNCH();
-    f64_to_bf16_pitched<<<gridn(ov * ov), 256, 0, s>>>(st.Kmat.p, ov, st.Jmat_bf.p + ovp, 4 * ovp, ov, ov);
-    EA_LAUNCH();
-    OpDst tA{st.tauA_bf.p, ovp}, tC{st.Kmat_bf.p + ovp, 2 * ovp}, tD{st.Jmat_bf.p + 3 * ovp, 4 * ovp},
-        m2C{st.Jmat_bf.p + 2 * ovp, 4 * ovp}, m2A{st.tm2A_bf.p, ovp}, tB{st.tm2A_bf.p + ov * ovp, ovp};
-    tau_operands<<<gridn(ov * ov), 256, 0, s>>>(st.tau.p, tA, tB, tC, tD, m2A, m2C, o, v);
+    st.tau32.alloc(st.tau.n, s);
+    f64_to_f32<<<gridn(st.tau.n), 256, 0, s>>>(st.tau.p, st.tau32.p, (long long)st.tau.n);
     EA_LAUNCH();
   }
   if (!st.err.p) {
@@ -227,6 +304,18 @@ void prepare_mixed(cudaStream_t s, State& st) {
     EA_LAUNCH();
   }
   st.mixed_ready = true;
+}
+
+// C (=, or += when g.reduce) A B^T; with low parts, the split products
+// A_hi B_hi + A_hi B_lo + A_lo B_hi accumulated by TMA reduce-add.
+void gemm_split(cudaStream_t s, const TmaMap& Ah, const TmaMap* Al, const TmaMap& Bh, const TmaMap* Bl,
+                const TmaMap& C, tc2::Args g) {
+  tc_gemm2(s, Ah, Bh, C, g);
+  if (Al && Bl) {
+    g.reduce = 1;
+    tc_gemm2(s, Ah, *Bl, C, g);
+    tc_gemm2(s, *Al, Bh, C, g);
+  }
 }
 
 tc2::Args gargs(int M, int N, int K, int* err) {
@@ -248,80 +337,121 @@ __global__ void compact_f32(const float* __restrict__ in, long long ip, float* _
 }  // namespace
 
 // Transposed ladder out[(nk,c)][b] (row pitch pad8(v)) = (sum_Q B^Q W_nk B^Q)[b][c]
-// for nmat pair matrices W (bf16, rows (nk,d), columns e, pitch pad8(v)).
+// for nmat pair matrices W (bf16, rows (nk,d), columns e, pitch pad8(v); Wl its
+// low part in split mode).
 //   stage 1 (batch Q x nk): Z[nk][c][Q][d] = sum_e B^Q[c][e] W_nk[d][e]
 //   stage 2 (one GEMM):     out[(nk,c)][b] (+)= sum_(Q,d) Z[(nk,c)][(Q,d)] B^Q[b][d]
 // Z rows hold qc blocks of pad8(v) columns (pads zero, matching the zero pads
-// of the b-major copy of B), chunk accumulation by TMA reduce-add.
-void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, int nmat, float* out) {
+// of the b-major copy of B); chunks accumulate by TMA reduce-add.  In split
+// mode Z is formed in FP32 by the three split products and split again.
+void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out) {
   const int v = st.v, naux = st.naux;
+  const bool x3 = Wlo != nullptr;
   const long long dp = pad8(v), bp = (long long)naux * dp;
-  // chunk of auxiliary functions: Z about 48M bf16 elements
-  int qc = (int)std::max<long long>(1, (48LL << 20) / std::max<long long>(1, (long long)nmat * v * dp));
+  // chunk of auxiliary functions: Z about 48M (split mode 24M) elements
+  const long long budget = x3 ? (24LL << 20) : (48LL << 20);
+  int qc = (int)std::max<long long>(1, budget / std::max<long long>(1, (long long)nmat * v * dp));
   qc = std::min(qc, naux);
-  DArr<bf16> Z((size_t)nmat * v * qc * dp, s);
-  if (dp != v) EA_CK(cudaMemsetAsync(Z.p, 0, Z.n * sizeof(bf16), s));
-  TmaMap mB3 = make_tma_3d(st.Bvv_bf.p, v, v, naux, dp, v * dp, 128);                  // stage-1 A: [Q][c][e]
+  const size_t zn = (size_t)nmat * v * qc * dp;
+  DArr<bf16> Z(zn, s), Zl;
+  DArr<float> Z32;
+  if (x3) {
+    Zl.alloc(zn, s);
+    Z32.alloc(zn, s);
+    if (dp != v) EA_CK(cudaMemsetAsync(Z32.p, 0, zn * sizeof(float), s));
+  } else if (dp != v) {
+    EA_CK(cudaMemsetAsync(Z.p, 0, zn * sizeof(bf16), s));
+  }
   const int bn = pick_bn(v);
-  TmaMap mW = make_tma_3d(Wbf, v, v, nmat, dp, (long long)v * dp, bn);                 // stage-1 B: [nk][d][e]
-  TmaMap mBb = make_tma_3d(st.Bb_bf.p, bp, v, 1, bp, bp * v, bn);                      // stage-2 B: [b][(Q,d)]
+  TmaMap mB3 = make_tma_3d(st.Bvv_bf.p, v, v, naux, dp, v * dp, 128);   // stage-1 A: [Q][c][e]
+  TmaMap mW = make_tma_3d(Wbf, v, v, nmat, dp, (long long)v * dp, bn);  // stage-1 B: [nk][d][e]
+  TmaMap mBb = make_tma_3d(st.Bb_bf.p, bp, v, 1, bp, bp * v, bn);       // stage-2 B: [b][(Q,d)]
+  TmaMap mB3l, mWl, mBbl;
+  if (x3) {
+    mB3l = make_tma_3d(st.Bvv_lo.p, v, v, naux, dp, v * dp, 128);
+    mWl = make_tma_3d(Wlo, v, v, nmat, dp, (long long)v * dp, bn);
+    mBbl = make_tma_3d(st.Bb_lo.p, bp, v, 1, bp, bp * v, bn);
+  }
   TmaMap mOut = make_tma_out4d(out, 4, v, 1, (long long)nmat * v, 1, dp, dp, (long long)nmat * v * dp);
   for (int Q0 = 0; Q0 < naux; Q0 += qc) {
     const int q = std::min(qc, naux - Q0);
-    TmaMap mZo = make_tma_out4d(Z.p, 2, v, q, v, nmat, dp, (long long)qc * dp, (long long)v * qc * dp);
     tc2::Args g1 = gargs(v, v, v, st.err.p);
     g1.nzlo = q; g1.nz = q * nmat;
     g1.a_sel = tc2::Z_LO; g1.a_z0 = Q0;
     g1.b_sel = tc2::Z_HI;
-    g1.out_bf16 = 1;
-    tc_gemm2(s, mB3, mW, mZo, g1);
+    if (!x3) {
+      TmaMap mZo = make_tma_out4d(Z.p, 2, v, q, v, nmat, dp, (long long)qc * dp, (long long)v * qc * dp);
+      g1.out_bf16 = 1;
+      tc_gemm2(s, mB3, mW, mZo, g1);
+    } else {
+      TmaMap mZo = make_tma_out4d(Z32.p, 4, v, q, v, nmat, dp, (long long)qc * dp, (long long)v * qc * dp);
+      gemm_split(s, mB3, &mB3l, mW, &mWl, mZo, g1);
+      split_f32<<<gridn((long long)zn), 256, 0, s>>>(Z32.p, Z.p, Zl.p, (long long)zn);
+      EA_LAUNCH();
+    }
     // K extent of this chunk exactly q*dp: columns past it read as zero
     TmaMap mZ = make_tma_3d(Z.p, (long long)q * dp, (long long)nmat * v, 1, (long long)qc * dp,
                             (long long)nmat * v * qc * dp, 128);
     tc2::Args g2 = gargs(nmat * v, v, (int)(q * dp), st.err.p);
     g2.b_k0 = (int)(Q0 * dp);
     g2.reduce = (Q0 > 0);
-    tc_gemm2(s, mZ, mBb, mOut, g2);
+    if (!x3) {
+      tc_gemm2(s, mZ, mBb, mOut, g2);
+    } else {
+      TmaMap mZl = make_tma_3d(Zl.p, (long long)q * dp, (long long)nmat * v, 1, (long long)qc * dp,
+                               (long long)nmat * v * qc * dp, 128);
+      gemm_split(s, mZ, &mZl, mBb, &mBbl, mOut, g2);
+    }
   }
 }
 
-void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y) {
+void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y, bool x3) {
   if (st.order < 3) {  // ADC(2): first-order coupling and diagonal only, no tensor-core terms
     sigma_base_fp64(s, st, nvec, x, y, false, false);
     return;
   }
-  prepare_mixed(s, st);
+  prepare_mixed(s, st, x3);
   const int o = st.o, v = st.v;
   const long long vv = (long long)v * v, ov = (long long)o * v, n2 = ov * v, dim = st.dim;
   const long long vp = pad8(v), ovp = pad8(ov), nv = (long long)nvec * v;
-  // FP64: orbital-energy diagonal, 1p/1p block, small coupling pieces and the DF intermediates F, G
+  // FP64: orbital-energy diagonal and 1p/1p block; FP32 (CUDA cores): the DF
+  // coupling pieces (first-order coupling, the o^3 v^2 term, F and G)
   diag_and_m11(s, st, nvec, x, y);
-  DArr<double> F((size_t)(nvec * n2), s), G((size_t)(nvec * n2), s), CA((size_t)n2, s);
+  const CoupOps<float> ops{o, v, st.naux, st.order, st.Boo32.p, st.Bov32.p, st.Bvv32.p, st.tau32.p};
+  DArr<float> x32((size_t)(nvec * dim), s);
+  f64_to_f32<<<gridn(nvec * dim), 256, 0, s>>>(x, x32.p, nvec * dim);
+  EA_LAUNCH();
+  DArr<float> F((size_t)(nvec * n2), s), G((size_t)(nvec * n2), s), CA((size_t)n2, s);
   for (int n = 0; n < nvec; ++n) {
-    couple_1p_to_2p1h(s, st, x + n * dim, CA.p, nullptr, false, F.p + n * n2, G.p + n * n2);
-    pair_combine(s, CA.p, vv, y + n * dim + v, vv, o, v, kS1, kS2, 1.0, 1.0);
+    couple12<float>(s, ops, x32.p + n * dim, CA.p, nullptr, false, F.p + n * n2, G.p + n * n2);
+    add_S_f32<<<gridn(n2), 256, 0, s>>>(CA.p, y + n * dim, o, v);
+    EA_LAUNCH();
   }
-  // BF16 operands
-  DArr<bf16> Wbf((size_t)(ov * nvec * vp), s);
-  pack_w_bf16<<<gridn(n2 * nvec), 256, 0, s>>>(x, Wbf.p, nvec, dim, v, n2, vp);
+  // BF16 operands (and low parts in split mode)
+  DArr<bf16> Wbf((size_t)(ov * nvec * vp), s), Wlo;
+  if (x3) Wlo.alloc(Wbf.n, s);
+  pack_w_bf16<<<gridn(n2 * nvec), 256, 0, s>>>(x, OpDst{Wbf.p, vp, x3 ? Wlo.p : nullptr}, nvec, dim, v, n2);
   EA_LAUNCH();
   DArr<bf16> B1((size_t)(nv * 2 * ovp), s), B2((size_t)(nv * 4 * ovp), s), BV1((size_t)(nv * ovp), s),
-      BV2((size_t)(nv * ovp), s);
+      BV2((size_t)(nv * ovp), s), B1l, B2l, BV1l, BV2l;
+  if (x3) { B1l.alloc(B1.n, s); B2l.alloc(B2.n, s); BV1l.alloc(BV1.n, s); BV2l.alloc(BV2.n, s); }
   if (ovp != ov) {
-    EA_CK(cudaMemsetAsync(B1.p, 0, B1.n * sizeof(bf16), s));
-    EA_CK(cudaMemsetAsync(B2.p, 0, B2.n * sizeof(bf16), s));
+    for (DArr<bf16>* a : {&B1, &B2, &B1l, &B2l})
+      if (a->p) EA_CK(cudaMemsetAsync(a->p, 0, a->n * sizeof(bf16), s));
   }
+  auto lo = [&](DArr<bf16>& a, long long o2) { return x3 ? a.p + o2 : nullptr; };
   // B1 = [AmT | F1], B2 = [BmT | AtT | G1 | F1]
-  ring_operands<<<gridn(nv * ov), 256, 0, s>>>(x, OpDst{B1.p, 2 * ovp}, OpDst{B2.p, 4 * ovp},
-                                                OpDst{B2.p + ovp, 4 * ovp}, OpDst{BV1.p, ovp}, OpDst{BV2.p, ovp},
-                                                nvec, dim, o, v);
+  ring_operands<<<gridn(nv * ov), 256, 0, s>>>(
+      x, OpDst{B1.p, 2 * ovp, lo(B1l, 0)}, OpDst{B2.p, 4 * ovp, lo(B2l, 0)}, OpDst{B2.p + ovp, 4 * ovp, lo(B2l, ovp)},
+      OpDst{BV1.p, ovp, lo(BV1l, 0)}, OpDst{BV2.p, ovp, lo(BV2l, 0)}, nvec, dim, o, v);
   EA_LAUNCH();
-  fg_operands<<<gridn(nvec * n2), 256, 0, s>>>(F.p, G.p, OpDst{B1.p + ovp, 2 * ovp}, OpDst{B2.p + 3 * ovp, 4 * ovp},
-                                               OpDst{B2.p + 2 * ovp, 4 * ovp}, nvec, o, v);
+  fg_operands<<<gridn(nvec * n2), 256, 0, s>>>(F.p, G.p, OpDst{B1.p + ovp, 2 * ovp, lo(B1l, ovp)},
+                                               OpDst{B2.p + 3 * ovp, 4 * ovp, lo(B2l, 3 * ovp)},
+                                               OpDst{B2.p + 2 * ovp, 4 * ovp, lo(B2l, 2 * ovp)}, nvec, o, v);
   EA_LAUNCH();
   // tensor-core GEMMs
   DArr<float> L((size_t)(ov * nvec * vp), s);
-  ladder_tc(s, st, Wbf.p, nvec * o, L.p);
+  ladder_tc(s, st, Wbf.p, x3 ? Wlo.p : nullptr, nvec * o, L.p);
   const long long nvp = pad8(nv);
   DArr<float> T1((size_t)(ov * nvp), s), T2((size_t)(ov * nvp), s), H1((size_t)(ov * nvp), s),
       H23((size_t)(2 * ov * nvp), s);
@@ -334,24 +464,40 @@ void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y
   TmaMap bT2 = make_tma_3d(B2.p, 4 * ovp, nv, 1, 4 * ovp, nv * 4 * ovp, bnn);
   TmaMap bV1 = make_tma_3d(BV1.p, ov, nv, 1, ovp, nv * ovp, bnn);
   TmaMap bV2 = make_tma_3d(BV2.p, ov, nv, 1, ovp, nv * ovp, bnn);
+  TmaMap aT1l, aT2l, aH1l, aH23l, bT1l, bT2l, bV1l, bV2l;
+  if (x3) {
+    aT1l = make_tma_3d(st.Kmat_lo.p, 2 * ovp, ov, 1, 2 * ovp, ov * 2 * ovp, 128);
+    aT2l = make_tma_3d(st.Jmat_lo.p, 4 * ovp, ov, 1, 4 * ovp, ov * 4 * ovp, 128);
+    aH1l = make_tma_3d(st.tauA_lo.p, ov, ov, 1, ovp, ov * ovp, 128);
+    aH23l = make_tma_3d(st.tm2A_lo.p, ov, 2 * ov, 1, ovp, 2 * ov * ovp, 128);
+    bT1l = make_tma_3d(B1l.p, 2 * ovp, nv, 1, 2 * ovp, nv * 2 * ovp, bnn);
+    bT2l = make_tma_3d(B2l.p, 4 * ovp, nv, 1, 4 * ovp, nv * 4 * ovp, bnn);
+    bV1l = make_tma_3d(BV1l.p, ov, nv, 1, ovp, nv * ovp, bnn);
+    bV2l = make_tma_3d(BV2l.p, ov, nv, 1, ovp, nv * ovp, bnn);
+  }
+  auto P = [&](TmaMap& m) { return x3 ? &m : nullptr; };
   auto outmap = [&](float* p, long long rows) { return make_tma_out4d(p, 4, nv, 1, rows, 1, nvp, nvp, rows * nvp); };
   tc2::Args g = gargs((int)ov, (int)nv, (int)(2 * ovp), st.err.p);
-  tc_gemm2(s, aT1, bT1, outmap(T1.p, ov), g);
+  gemm_split(s, aT1, P(aT1l), bT1, P(bT1l), outmap(T1.p, ov), g);
   g.K = (int)(4 * ovp);
-  tc_gemm2(s, aT2, bT2, outmap(T2.p, ov), g);
+  gemm_split(s, aT2, P(aT2l), bT2, P(bT2l), outmap(T2.p, ov), g);
   g.K = (int)ov;
-  tc_gemm2(s, aH1, bV1, outmap(H1.p, ov), g);
+  gemm_split(s, aH1, P(aH1l), bV1, P(bV1l), outmap(H1.p, ov), g);
   g.M = (int)(2 * ov);
-  tc_gemm2(s, aH23, bV2, outmap(H23.p, 2 * ov), g);
+  gemm_split(s, aH23, P(aH23l), bV2, P(bV2l), outmap(H23.p, 2 * ov), g);
   combine_ring_ladder<<<gridn(n2 * nvec), 256, 0, s>>>(y, T1.p, T2.p, L.p, nvec, dim, o, v, nvp, vp);
   EA_LAUNCH();
-  // 2p1h -> 1p finishing in FP64 from the tensor-core H tensors
-  DArr<double> h1((size_t)(nvec * n2), s), h2((size_t)(nvec * n2), s), h3((size_t)(nvec * n2), s), V((size_t)n2, s);
+  // 2p1h -> 1p finishing (FP32, CUDA cores) from the tensor-core H tensors
+  DArr<float> h1((size_t)(nvec * n2), s), h2((size_t)(nvec * n2), s), h3((size_t)(nvec * n2), s), V((size_t)n2, s),
+      sy((size_t)v, s);
   h_from_tc<<<gridn(nvec * n2), 256, 0, s>>>(H1.p, H23.p, h1.p, h2.p, h3.p, nvec, o, v, nvp);
   EA_LAUNCH();
   for (int n = 0; n < nvec; ++n) {
-    pair_combine(s, x + n * dim + v, vv, V.p, vv, o, v, kS1, kS2, 1.0, 0.0);
-    couple_2p1h_to_1p(s, st, V.p, y + n * dim, nullptr, h1.p + n * n2, h2.p + n * n2, h3.p + n * n2);
+    pair_combineT<float>(s, x32.p + n * dim + v, vv, V.p, vv, o, v, (float)kS1, (float)kS2, 1.f, 0.f);
+    fillT<float>(s, sy.p, (size_t)v, 0.f);
+    couple21<float>(s, ops, V.p, sy.p, nullptr, h1.p + n * n2, h2.p + n * n2, h3.p + n * n2);
+    add_f32<<<gridn(v), 256, 0, s>>>(sy.p, y + n * dim, v);
+    EA_LAUNCH();
   }
 }
 
@@ -360,16 +506,16 @@ void ladder_only(cudaStream_t s, State& st, int nvec, const double* x, float* ou
   const int o = st.o, v = st.v;
   const long long ov = (long long)o * v, n2 = ov * v;
   if (!mixed) fail(EAADC_ERR_ARG, "ladder_only: tensor-core path only");
-  prepare_mixed(s, st);
+  prepare_mixed(s, st, st.x3_ready);
   const long long vp = pad8(v);
   DArr<bf16> Wbf((size_t)(ov * nvec * vp), s);
-  pack_w_bf16<<<gridn(n2 * nvec), 256, 0, s>>>(x, Wbf.p, nvec, st.dim, v, n2, vp);
+  pack_w_bf16<<<gridn(n2 * nvec), 256, 0, s>>>(x, OpDst{Wbf.p, vp, nullptr}, nvec, st.dim, v, n2);
   EA_LAUNCH();
   if (vp == v) {
-    ladder_tc(s, st, Wbf.p, nvec * o, out);
+    ladder_tc(s, st, Wbf.p, nullptr, nvec * o, out);
   } else {
     DArr<float> L((size_t)(ov * nvec * vp), s);
-    ladder_tc(s, st, Wbf.p, nvec * o, L.p);
+    ladder_tc(s, st, Wbf.p, nullptr, nvec * o, L.p);
     compact_f32<<<gridn(n2 * nvec), 256, 0, s>>>(L.p, vp, out, ov * nvec, v);
     EA_LAUNCH();
   }

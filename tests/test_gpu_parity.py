@@ -180,6 +180,15 @@ def test_mixed_sigma_vs_fp64(E, o, v, naux, decay, seed):
         assert np.abs(smx - s64).max() <= 2e-2 * scale
         # the 1p part only sees BF16 through the second-order coupling contractions
         assert np.abs(smx[:, :v] - s64[:, :v]).max() <= 1e-4 * np.abs(s64[:, :v]).max()
+        # split-BF16: each operand carries ~16 significant bits (representation
+        # error <= 2^-17 relative), the dropped lo*lo product is ~2^-18, and the
+        # re-split stage-1 intermediate adds the same again: 2e-4 of the scale
+        sx3 = E.eaadc_sigma_host(ctx, 0, x, E.EAADC_MIXED_BF16X3)
+        err3 = np.abs(sx3 - s64).max()
+        print(f"mixed err {np.abs(smx - s64).max() / scale:.2e}  x3 err {err3 / scale:.2e}")
+        assert err3 <= 2e-4 * scale
+        # a BF16 sigma after an x3 one rebuilds nothing and stays as before
+        assert np.array_equal(E.eaadc_sigma_host(ctx, 0, x, E.EAADC_MIXED_BF16), smx)
     finally:
         E.eaadc_destroy(ctx)
 
@@ -194,17 +203,23 @@ def test_mixed_davidson_tiny(E):
         assert np.abs(om[0] - ref).max() <= 1e-5       # reduced-precision target
         om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-8, prec=E.EAADC_MIXED_BF16, refine=1)
         assert st == 0 and np.abs(om[0] - ref).max() <= 1e-8  # after FP64 refinement
+        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-6, prec=E.EAADC_MIXED_BF16X3, refine=0)
+        assert np.abs(om[0] - ref).max() <= 1e-7       # split-BF16 target
+        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-8, prec=E.EAADC_MIXED_BF16X3, refine=1)
+        assert st == 0 and np.abs(om[0] - ref).max() <= 1e-8
     finally:
         E.eaadc_destroy(ctx)
 
 
 @pytest.mark.skipif(not os.path.exists(os.path.join(GOLD, "canonical-200.npz")), reason="golden file missing")
-def test_canonical_200_mixed_refined_against_oracle(E):
+@pytest.mark.parametrize("prec", ["EAADC_MIXED_BF16", "EAADC_MIXED_BF16X3"])
+def test_canonical_200_mixed_refined_against_oracle(E, prec):
     g = np.load(os.path.join(GOLD, "canonical-200.npz"))
     pr = config_problem("canonical-200")
     ctx = _ctx(E, pr)
     try:
-        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-7, prec=E.EAADC_MIXED_BF16, refine=1)
+        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-7, prec=getattr(E, prec), refine=1, max_sub=40, maxit=300)
+        print(f"{prec}: iters {it[0]} resnorm {rn[0].max():.1e}")
         assert st == 0
         assert np.abs(om[0] - g["omega3"]).max() <= 1e-8
     finally:
