@@ -126,6 +126,47 @@ eaadc_status eaadc_sigma_host(eaadc_ctx* ctx, int state, int nvec, const double*
 eaadc_status eaadc_ladder(eaadc_ctx* ctx, int state, int nvec, const double* x_dev, float* out_dev,
                           void* stream);
 
+/* Size in bytes of the one fixed device array that eaadc_ladder_noalloc works
+ * in.  Every GPU that loads this library holds it until the process exits. */
+#define EAADC_LADDER_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* eaadc_ladder that allocates no device memory.  The paper has no counterpart:
+ * this is a service to callers that cannot allocate at the point of the call.
+ * eaadc_ladder takes its working memory from the stream-ordered allocator on
+ * every call; a process whose device memory already belongs to its own memory
+ * manager (a framework's caching allocator, a server that reserves HBM at
+ * start-up) may see that fail or force its manager to give memory back, and a
+ * cudaFree synchronises the whole device, stalling the caller's other streams.
+ * This entry point instead works in one fixed array of
+ * EAADC_LADDER_NOALLOC_SCRATCH_BYTES and calls no allocator.
+ *
+ * Arguments, output layout and arithmetic are those of eaadc_ladder (the sum
+ * over auxiliary functions is cut into blocks that fit the array, so results
+ * agree with it to FP32 rounding).  out_dev must be 16-byte aligned.
+ *
+ * Limit: the BF16 copy of the 2p1h vectors (nvec*o*v'*pad8(v')*2 bytes), for
+ * v' not a multiple of 8 an FP32 copy of the result (nvec*o*v'*pad8(v')*4
+ * bytes), and the intermediate of one auxiliary function (again
+ * nvec*o*v'*pad8(v')*2 bytes) must fit in the array; larger nvec is rejected
+ * with EAADC_ERR_ARG and the sizes in eaadc_last_error (o=20, v'=200 allows
+ * up to 10 vectors per call).
+ *
+ * Preconditions: the state's BF16 operands must exist; the first eaadc_ladder
+ * or reduced-precision eaadc_sigma on the state makes them (those calls do
+ * allocate).  Otherwise EAADC_ERR_STATE.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (with that device current) and keeps it.  Make that first call before any
+ * stream capture on the device.
+ *
+ * Sharing: all calls on one device, from any context or thread, use the same
+ * array, and it keeps what the last call left there; each call clears the
+ * parts that must start at zero.  Calls whose GPU work can overlap (different
+ * streams or contexts with no ordering between them) race on the array and
+ * give wrong results: order them on one stream or with events. */
+eaadc_status eaadc_ladder_noalloc(eaadc_ctx* ctx, int state, int nvec, const double* x_dev,
+                                  float* out_dev, void* stream);
+
 /* Davidson diagonal preconditioner values D (host [dim]): D_a = M_aa for the
  * 1p part, e_b + e_c - e_k for the 2p1h part. */
 eaadc_status eaadc_diagonal(eaadc_ctx* ctx, int state, double* diag_host);

@@ -28,6 +28,7 @@ EXPORTED = (
     "eaadc_version", "eaadc_init", "eaadc_build_canonical", "eaadc_state_info", "eaadc_sigma",
     "eaadc_sigma_host", "eaadc_diagonal", "eaadc_get_m11", "eaadc_davidson", "eaadc_get_eigvecs",
     "eaadc_destroy", "eaadc_last_error", "eaadc_ladder", "eaadc_kernel_launches",
+    "eaadc_ladder_noalloc",
 )
 
 
@@ -61,6 +62,7 @@ def lib():
         L.eaadc_sigma_host.argtypes = [vp, C.c_int, C.c_int, dp, dp, C.c_int]
         L.eaadc_diagonal.argtypes = [vp, C.c_int, dp]
         L.eaadc_ladder.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
+        L.eaadc_ladder_noalloc.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
         L.eaadc_get_m11.argtypes = [vp, C.c_int, dp]
         L.eaadc_davidson.argtypes = [vp, C.c_int, C.POINTER(DavidsonOpts), dp, dp, ip]
         L.eaadc_get_eigvecs.argtypes = [vp, C.c_int, dp]
@@ -136,6 +138,12 @@ def eaadc_sigma_host(ctx, state, x, prec=EAADC_FP64):
 def eaadc_ladder(ctx, state, nvec, x_ptr, out_ptr, stream=None):
     """Device pointers: x [nvec][dim] float64, out [nvec][o][v][v] float32."""
     _check(ctx, lib().eaadc_ladder(ctx, state, nvec, C.c_void_p(x_ptr), C.c_void_p(out_ptr), stream))
+
+
+def eaadc_ladder_noalloc(ctx, state, nvec, x_ptr, out_ptr, stream=None):
+    """As eaadc_ladder, working in the library's fixed device array instead of
+    allocating (for callers that cannot allocate device memory mid-run)."""
+    _check(ctx, lib().eaadc_ladder_noalloc(ctx, state, nvec, C.c_void_p(x_ptr), C.c_void_p(out_ptr), stream))
 
 
 def eaadc_diagonal(ctx, state=0):
