@@ -144,12 +144,12 @@ eaadc_status eaadc_ladder(eaadc_ctx* ctx, int state, int nvec, const double* x_d
  * over auxiliary functions is cut into blocks that fit the array, so results
  * agree with it to FP32 rounding).  out_dev must be 16-byte aligned.
  *
- * Limit: the BF16 copy of the 2p1h vectors (nvec*o*v'*pad8(v')*2 bytes), for
- * v' not a multiple of 8 an FP32 copy of the result (nvec*o*v'*pad8(v')*4
- * bytes), and the intermediate of one auxiliary function (again
- * nvec*o*v'*pad8(v')*2 bytes) must fit in the array; larger nvec is rejected
- * with EAADC_ERR_ARG and the sizes in eaadc_last_error (o=20, v'=200 allows
- * up to 10 vectors per call).
+ * Limit: with r64(n) = n rounded up to a multiple of 64, the BF16 copy of the
+ * 2p1h vectors (nvec*o*v'*r64(v')*2 bytes), for v' not a multiple of 4 an FP32
+ * copy of the result (about nvec*o*v'*v'*4 bytes), and the intermediate of one
+ * auxiliary function (nvec*o*v'*r64(pad8(v'))*2 bytes) must fit in the array;
+ * larger nvec is rejected with EAADC_ERR_ARG and the sizes in
+ * eaadc_last_error (o=20, v'=200 allows up to 8 vectors per call).
  *
  * Preconditions: the state's BF16 operands must exist; the first eaadc_ladder
  * or reduced-precision eaadc_sigma on the state makes them (those calls do

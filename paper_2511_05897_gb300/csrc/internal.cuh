@@ -153,6 +153,7 @@ struct State {
   DArr<float> Boo32, Bov32, Bvv32, tau32;     // FP32 copies for the DF coupling pieces
   DArr<bf16> Bvv_lo, Bb_lo, Kmat_lo, Jmat_lo, tauA_lo, tm2A_lo;  // low parts (split-BF16 mode)
   bool x3_ready = false;
+  long long bvv_pitch = 0, bb_pitch = 0;      // row pitches (elements) of Bvv_bf and Bb_bf
   DArr<int> err;                              // device error word of bounded waits
   bool mixed_ready = false;
   // last Davidson solution

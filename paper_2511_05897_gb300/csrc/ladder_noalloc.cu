@@ -51,24 +51,26 @@ void* scratch_address(int dev) {
 
 size_t round256(size_t n) { return (n + 255) / 256 * 256; }
 long long pad8(long long n) { return (n + 7) / 8 * 8; }
+long long rp64(long long n) { return (n + 63) / 64 * 64; }  // BF16 row pitch: whole 128-byte lines
+long long rp32(long long n) { return (n + 31) / 32 * 32; }  // FP32 row pitch: whole 128-byte lines
 int grid_for(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
 
-// W[(n,k,d)][e] (row pitch dp) = bf16(x[n][v + (k,d,e)])
+// W[(n,k,d)][e] (row pitch wp) = bf16(x[n][v + (k,d,e)])
 __global__ void noalloc_pack_w(const double* __restrict__ x, bf16* __restrict__ W, int nvec, long long dim, int v,
-                               long long n2, long long dp) {
+                               long long n2, long long wp) {
   const long long total = n2 * nvec;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long n = i / n2, r = i % n2;
-    W[(i / v) * dp + i % v] = __float2bfloat16_rn((float)x[n * dim + v + r]);
+    W[(i / v) * wp + i % v] = __float2bfloat16_rn((float)x[n * dim + v + r]);
   }
 }
 
-// out[r][c] (row pitch v) = L[r][c] (row pitch dp), c < v
-__global__ void noalloc_compact(const float* __restrict__ L, long long dp, float* __restrict__ out, long long rows,
+// out[r][c] (row pitch v) = L[r][c] (row pitch lp), c < v
+__global__ void noalloc_compact(const float* __restrict__ L, long long lp, float* __restrict__ out, long long rows,
                                 int v) {
   const long long total = rows * v;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
-    out[i] = L[(i / v) * dp + i % v];
+    out[i] = L[(i / v) * lp + i % v];
 }
 
 tc2::Args plain_args(int M, int N, int K, int* err) {
@@ -84,32 +86,37 @@ tc2::Args plain_args(int M, int N, int K, int* err) {
 void ladder_noalloc(cudaStream_t s, ea::State& st, int nvec, const double* x, float* out, unsigned char* base) {
   using namespace ea;
   const int o = st.o, v = st.v, naux = st.naux;
-  const long long dp = pad8(v), bp = (long long)naux * dp;
+  const long long dp = pad8(v), wp = rp64(v), lp = rp32(v), bk = (long long)naux * dp;
+  const long long bvp = st.bvv_pitch, bbp = st.bb_pitch;
   const long long nmat = (long long)nvec * o, n2 = (long long)o * v * v;
-  // scratch layout: [W bf16 nmat*v*dp] [L fp32 nmat*v*dp, only if dp != v] [Z bf16 nmat*v*qc*dp]
-  const size_t wbytes = round256((size_t)(nmat * v * dp) * sizeof(bf16));
-  const size_t lbytes = dp != v ? round256((size_t)(nmat * v * dp) * sizeof(float)) : 0;
-  const size_t zq = (size_t)(nmat * v * dp) * sizeof(bf16);  // one auxiliary function of Z
-  if (wbytes + lbytes + zq > kScratchBytes)
+  const bool staged = v % 4 != 0;  // rows of out are not whole 16-byte units: stage the result
+  // scratch layout: [W bf16 nmat*v*wp] [L fp32 nmat*v*lp, if staged] [Z bf16 nmat*v*zp]
+  const size_t wbytes = round256((size_t)(nmat * v * wp) * sizeof(bf16));
+  const size_t lbytes = staged ? round256((size_t)(nmat * v * lp) * sizeof(float)) : 0;
+  auto zbytes = [&](long long q) { return (size_t)(nmat * v * rp64(q * dp)) * sizeof(bf16); };
+  if (wbytes + lbytes + zbytes(1) > kScratchBytes)
     fail(EAADC_ERR_ARG, "ladder_noalloc: " + std::to_string(nvec) + " vectors need at least " +
-                            std::to_string(wbytes + lbytes + zq) + " bytes of scratch, the fixed limit is " +
+                            std::to_string(wbytes + lbytes + zbytes(1)) + " bytes of scratch, the fixed limit is " +
                             std::to_string(kScratchBytes) + " (use fewer vectors per call, or eaadc_ladder)");
-  const int qc = (int)std::min<long long>(naux, (long long)((kScratchBytes - wbytes - lbytes) / zq));
+  const size_t zroom = kScratchBytes - wbytes - lbytes;
+  int qc = (int)std::min<long long>(naux, (long long)(zroom / ((size_t)(nmat * v * dp) * sizeof(bf16))));
+  while (qc > 1 && zbytes(qc) > zroom) --qc;
+  const long long zp = rp64((long long)qc * dp);  // Z row pitch
   bf16* W = reinterpret_cast<bf16*>(base);
-  float* L = dp != v ? reinterpret_cast<float*>(base + wbytes) : out;
+  float* L = staged ? reinterpret_cast<float*>(base + wbytes) : out;
+  const long long op = staged ? lp : v;
   bf16* Z = reinterpret_cast<bf16*>(base + wbytes + lbytes);
-  const long long zn = nmat * v * qc * dp;
   // Stage 1 writes only the v real columns of each dp-wide block of Z, and
   // stage 2 reads the pads: they must be zero, not what the last call left.
-  if (dp != v) EA_CK(cudaMemsetAsync(Z, 0, (size_t)zn * sizeof(bf16), s));
+  if (dp != v) EA_CK(cudaMemsetAsync(Z, 0, zbytes(qc), s));
 
-  noalloc_pack_w<<<grid_for(n2 * nvec), 256, 0, s>>>(x, W, nvec, st.dim, v, n2, dp);
+  noalloc_pack_w<<<grid_for(n2 * nvec), 256, 0, s>>>(x, W, nvec, st.dim, v, n2, wp);
   EA_LAUNCH();
   const int bn = pick_bn(v);
-  TmaMap mB3 = make_tma_3d(st.Bvv_bf.p, v, v, naux, dp, v * dp, 128);   // stage-1 A: B^Q [Q][c][e]
-  TmaMap mW = make_tma_3d(W, v, v, nmat, dp, (long long)v * dp, bn);     // stage-1 B: W [nk][d][e]
-  TmaMap mBb = make_tma_3d(st.Bb_bf.p, bp, v, 1, bp, bp * v, bn);        // stage-2 B: [b][(Q,d)]
-  TmaMap mOut = make_tma_out4d(L, 4, v, 1, nmat * v, 1, dp, dp, nmat * v * dp);
+  TmaMap mB3 = make_tma_3d(st.Bvv_bf.p, v, v, naux, bvp, v * bvp, 128);  // stage-1 A: B^Q [Q][c][e]
+  TmaMap mW = make_tma_3d(W, v, v, nmat, wp, (long long)v * wp, bn);     // stage-1 B: W [nk][d][e]
+  TmaMap mBb = make_tma_3d(st.Bb_bf.p, bk, v, 1, bbp, bbp * v, bn);      // stage-2 B: [b][(Q,d)]
+  TmaMap mOut = make_tma_out4d(L, 4, v, 1, nmat * v, 1, op, op, nmat * v * op);
   for (int Q0 = 0; Q0 < naux; Q0 += qc) {
     const int q = std::min(qc, naux - Q0);
     // stage 1: Z[nk][c][Q][d] = sum_e B^Q[c][e] W_nk[d][e] for Q in [Q0, Q0+q)
@@ -118,17 +125,17 @@ void ladder_noalloc(cudaStream_t s, ea::State& st, int nvec, const double* x, fl
     g1.a_sel = tc2::Z_LO; g1.a_z0 = Q0;
     g1.b_sel = tc2::Z_HI;
     g1.out_bf16 = 1;
-    TmaMap mZo = make_tma_out4d(Z, 2, v, q, v, nmat, dp, (long long)qc * dp, (long long)v * qc * dp);
+    TmaMap mZo = make_tma_out4d(Z, 2, v, q, v, nmat, dp, zp, (long long)v * zp);
     tc_gemm2(s, mB3, mW, mZo, g1);
     // stage 2: L[(nk,c)][b] (+)= sum_(Q,d) Z[(nk,c)][(Q,d)] B^Q[b][d]
-    TmaMap mZ = make_tma_3d(Z, (long long)q * dp, nmat * v, 1, (long long)qc * dp, nmat * v * qc * dp, 128);
+    TmaMap mZ = make_tma_3d(Z, (long long)q * dp, nmat * v, 1, zp, nmat * v * zp, 128);
     tc2::Args g2 = plain_args((int)(nmat * v), v, (int)(q * dp), st.err.p);
     g2.b_k0 = (int)(Q0 * dp);
     g2.reduce = Q0 > 0;
     tc_gemm2(s, mZ, mBb, mOut, g2);
   }
-  if (dp != v) {
-    noalloc_compact<<<grid_for(n2 * nvec), 256, 0, s>>>(L, dp, out, nmat * v, v);
+  if (staged) {
+    noalloc_compact<<<grid_for(n2 * nvec), 256, 0, s>>>(L, lp, out, nmat * v, v);
     EA_LAUNCH();
   }
 }

@@ -37,6 +37,10 @@ const double kI2 = 0.5 * (1.0 - 0.57735026918962576451);
 
 int gridn(long long n) { return (int)std::min<long long>((n + 255) / 256, 152LL * 32); }
 long long pad8(long long n) { return (n + 7) / 8 * 8; }
+// Row pitches of TMA operands are whole 128-byte lines (64 BF16 or 32 FP32
+// elements), so that no box row straddles two L2 lines.
+long long rp64(long long n) { return (n + 63) / 64 * 64; }
+long long rp32(long long n) { return (n + 31) / 32 * 32; }
 
 // BF16 destination (row pitch in elements); lo, when set, receives the low
 // part x - bf16(x) at the same position.
@@ -233,14 +237,14 @@ __global__ void add_f32(const float* __restrict__ a, double* __restrict__ y, lon
 void convert_state_operands(cudaStream_t s, State& st, bool lo) {
   const int o = st.o, v = st.v, naux = st.naux;
   const long long vv = (long long)v * v, ov = (long long)o * v;
-  const long long vp = pad8(v), bp = (long long)naux * vp, ovp = pad8(ov);
+  const long long vp = pad8(v), ovp = rp64(ov);
   auto L = [&](DArr<bf16>& a) { return lo ? a.p : nullptr; };
   auto zero = [&](DArr<bf16>& a) { EA_CK(cudaMemsetAsync(a.p, 0, a.n * sizeof(bf16), s)); };
-  f64_to_bf16_pitched<<<gridn(naux * vv), 256, 0, s>>>(st.Bvv.p, v, OpDst{st.Bvv_bf.p, vp, L(st.Bvv_lo)},
+  f64_to_bf16_pitched<<<gridn(naux * vv), 256, 0, s>>>(st.Bvv.p, v, OpDst{st.Bvv_bf.p, st.bvv_pitch, L(st.Bvv_lo)},
                                                       (long long)naux * v, v);
   EA_LAUNCH();
   if (vp != v) { zero(st.Bb_bf); if (lo) zero(st.Bb_lo); }
-  bmajor_bf16<<<gridn(naux * vv), 256, 0, s>>>(st.Bvv.p, OpDst{st.Bb_bf.p, bp, L(st.Bb_lo)}, naux, v, vp);
+  bmajor_bf16<<<gridn(naux * vv), 256, 0, s>>>(st.Bvv.p, OpDst{st.Bb_bf.p, st.bb_pitch, L(st.Bb_lo)}, naux, v, vp);
   EA_LAUNCH();
   if (st.order < 3) return;
   zero(st.Kmat_bf); zero(st.Jmat_bf); zero(st.tauA_bf); zero(st.tm2A_bf);
@@ -266,15 +270,17 @@ void convert_state_operands(cudaStream_t s, State& st, bool lo) {
 void prepare_mixed(cudaStream_t s, State& st, bool x3) {
   const int o = st.o, v = st.v, naux = st.naux;
   const long long ov = (long long)o * v;
-  const long long vp = pad8(v), bp = (long long)naux * vp, ovp = pad8(ov);
+  const long long vp = pad8(v), ovp = rp64(ov);
   if (x3 && st.mixed_ready && !st.x3_ready) st.mixed_ready = false;  // redo with low parts
   if (st.mixed_ready) return;
+  st.bvv_pitch = rp64(v);
+  st.bb_pitch = rp64((long long)naux * vp);
   auto alloc_pair = [&](DArr<bf16>& hi, DArr<bf16>& lo, size_t n) {
     hi.alloc(n, s);
     if (x3) lo.alloc(n, s);
   };
-  alloc_pair(st.Bvv_bf, st.Bvv_lo, (size_t)(naux * v * vp));
-  alloc_pair(st.Bb_bf, st.Bb_lo, (size_t)(v * bp));
+  alloc_pair(st.Bvv_bf, st.Bvv_lo, (size_t)(naux * v * st.bvv_pitch));
+  alloc_pair(st.Bb_bf, st.Bb_lo, (size_t)(v * st.bb_pitch));
   if (st.order >= 3) {
     alloc_pair(st.Kmat_bf, st.Kmat_lo, (size_t)(ov * 2 * ovp));
     alloc_pair(st.Jmat_bf, st.Jmat_lo, (size_t)(ov * 4 * ovp));
@@ -336,23 +342,26 @@ __global__ void compact_f32(const float* __restrict__ in, long long ip, float* _
 }
 }  // namespace
 
-// Transposed ladder out[(nk,c)][b] (row pitch pad8(v)) = (sum_Q B^Q W_nk B^Q)[b][c]
-// for nmat pair matrices W (bf16, rows (nk,d), columns e, pitch pad8(v); Wl its
-// low part in split mode).
+// Transposed ladder out[(nk,c)][b] (row pitch op, FP32) = (sum_Q B^Q W_nk B^Q)[b][c]
+// for nmat pair matrices W (bf16, rows (nk,d), columns e, row pitch rp64(v); Wl
+// its low part in split mode).
 //   stage 1 (batch Q x nk): Z[nk][c][Q][d] = sum_e B^Q[c][e] W_nk[d][e]
 //   stage 2 (one GEMM):     out[(nk,c)][b] (+)= sum_(Q,d) Z[(nk,c)][(Q,d)] B^Q[b][d]
 // Z rows hold qc blocks of pad8(v) columns (pads zero, matching the zero pads
 // of the b-major copy of B); chunks accumulate by TMA reduce-add.  In split
 // mode Z is formed in FP32 by the three split products and split again.
-void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out) {
+void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out, long long op) {
   const int v = st.v, naux = st.naux;
   const bool x3 = Wlo != nullptr;
-  const long long dp = pad8(v), bp = (long long)naux * dp;
-  // chunk of auxiliary functions: Z about 48M (split mode 24M) elements
+  const long long dp = pad8(v), wp = rp64(v), bk = (long long)naux * dp;
+  const long long bvp = st.bvv_pitch, bbp = st.bb_pitch;
+  // chunk of auxiliary functions: Z about 48M (split mode 24M) elements, so
+  // that it stays in L2 between the two stages
   const long long budget = x3 ? (24LL << 20) : (48LL << 20);
   int qc = (int)std::max<long long>(1, budget / std::max<long long>(1, (long long)nmat * v * dp));
   qc = std::min(qc, naux);
-  const size_t zn = (size_t)nmat * v * qc * dp;
+  const long long zp = rp64((long long)qc * dp);  // Z row pitch
+  const size_t zn = (size_t)nmat * v * zp;
   DArr<bf16> Z(zn, s), Zl;
   DArr<float> Z32;
   if (x3) {
@@ -363,16 +372,16 @@ void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int 
     EA_CK(cudaMemsetAsync(Z.p, 0, zn * sizeof(bf16), s));
   }
   const int bn = pick_bn(v);
-  TmaMap mB3 = make_tma_3d(st.Bvv_bf.p, v, v, naux, dp, v * dp, 128);   // stage-1 A: [Q][c][e]
-  TmaMap mW = make_tma_3d(Wbf, v, v, nmat, dp, (long long)v * dp, bn);  // stage-1 B: [nk][d][e]
-  TmaMap mBb = make_tma_3d(st.Bb_bf.p, bp, v, 1, bp, bp * v, bn);       // stage-2 B: [b][(Q,d)]
+  TmaMap mB3 = make_tma_3d(st.Bvv_bf.p, v, v, naux, bvp, v * bvp, 128);  // stage-1 A: [Q][c][e]
+  TmaMap mW = make_tma_3d(Wbf, v, v, nmat, wp, (long long)v * wp, bn);   // stage-1 B: [nk][d][e]
+  TmaMap mBb = make_tma_3d(st.Bb_bf.p, bk, v, 1, bbp, bbp * v, bn);      // stage-2 B: [b][(Q,d)]
   TmaMap mB3l, mWl, mBbl;
   if (x3) {
-    mB3l = make_tma_3d(st.Bvv_lo.p, v, v, naux, dp, v * dp, 128);
-    mWl = make_tma_3d(Wlo, v, v, nmat, dp, (long long)v * dp, bn);
-    mBbl = make_tma_3d(st.Bb_lo.p, bp, v, 1, bp, bp * v, bn);
+    mB3l = make_tma_3d(st.Bvv_lo.p, v, v, naux, bvp, v * bvp, 128);
+    mWl = make_tma_3d(Wlo, v, v, nmat, wp, (long long)v * wp, bn);
+    mBbl = make_tma_3d(st.Bb_lo.p, bk, v, 1, bbp, bbp * v, bn);
   }
-  TmaMap mOut = make_tma_out4d(out, 4, v, 1, (long long)nmat * v, 1, dp, dp, (long long)nmat * v * dp);
+  TmaMap mOut = make_tma_out4d(out, 4, v, 1, (long long)nmat * v, 1, op, op, (long long)nmat * v * op);
   for (int Q0 = 0; Q0 < naux; Q0 += qc) {
     const int q = std::min(qc, naux - Q0);
     tc2::Args g1 = gargs(v, v, v, st.err.p);
@@ -380,26 +389,24 @@ void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int 
     g1.a_sel = tc2::Z_LO; g1.a_z0 = Q0;
     g1.b_sel = tc2::Z_HI;
     if (!x3) {
-      TmaMap mZo = make_tma_out4d(Z.p, 2, v, q, v, nmat, dp, (long long)qc * dp, (long long)v * qc * dp);
+      TmaMap mZo = make_tma_out4d(Z.p, 2, v, q, v, nmat, dp, zp, (long long)v * zp);
       g1.out_bf16 = 1;
       tc_gemm2(s, mB3, mW, mZo, g1);
     } else {
-      TmaMap mZo = make_tma_out4d(Z32.p, 4, v, q, v, nmat, dp, (long long)qc * dp, (long long)v * qc * dp);
+      TmaMap mZo = make_tma_out4d(Z32.p, 4, v, q, v, nmat, dp, zp, (long long)v * zp);
       gemm_split(s, mB3, &mB3l, mW, &mWl, mZo, g1);
       split_f32<<<gridn((long long)zn), 256, 0, s>>>(Z32.p, Z.p, Zl.p, (long long)zn);
       EA_LAUNCH();
     }
     // K extent of this chunk exactly q*dp: columns past it read as zero
-    TmaMap mZ = make_tma_3d(Z.p, (long long)q * dp, (long long)nmat * v, 1, (long long)qc * dp,
-                            (long long)nmat * v * qc * dp, 128);
+    TmaMap mZ = make_tma_3d(Z.p, (long long)q * dp, (long long)nmat * v, 1, zp, (long long)nmat * v * zp, 128);
     tc2::Args g2 = gargs(nmat * v, v, (int)(q * dp), st.err.p);
     g2.b_k0 = (int)(Q0 * dp);
     g2.reduce = (Q0 > 0);
     if (!x3) {
       tc_gemm2(s, mZ, mBb, mOut, g2);
     } else {
-      TmaMap mZl = make_tma_3d(Zl.p, (long long)q * dp, (long long)nmat * v, 1, (long long)qc * dp,
-                               (long long)nmat * v * qc * dp, 128);
+      TmaMap mZl = make_tma_3d(Zl.p, (long long)q * dp, (long long)nmat * v, 1, zp, (long long)nmat * v * zp, 128);
       gemm_split(s, mZ, &mZl, mBb, &mBbl, mOut, g2);
     }
   }
@@ -413,7 +420,7 @@ void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y
   prepare_mixed(s, st, x3);
   const int o = st.o, v = st.v;
   const long long vv = (long long)v * v, ov = (long long)o * v, n2 = ov * v, dim = st.dim;
-  const long long vp = pad8(v), ovp = pad8(ov), nv = (long long)nvec * v;
+  const long long wp = rp64(v), lp = rp32(v), ovp = rp64(ov), nv = (long long)nvec * v;
   // FP64: orbital-energy diagonal and 1p/1p block; FP32 (CUDA cores): the DF
   // coupling pieces (first-order coupling, the o^3 v^2 term, F and G)
   diag_and_m11(s, st, nvec, x, y);
@@ -428,9 +435,9 @@ void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y
     EA_LAUNCH();
   }
   // BF16 operands (and low parts in split mode)
-  DArr<bf16> Wbf((size_t)(ov * nvec * vp), s), Wlo;
+  DArr<bf16> Wbf((size_t)(ov * nvec * wp), s), Wlo;
   if (x3) Wlo.alloc(Wbf.n, s);
-  pack_w_bf16<<<gridn(n2 * nvec), 256, 0, s>>>(x, OpDst{Wbf.p, vp, x3 ? Wlo.p : nullptr}, nvec, dim, v, n2);
+  pack_w_bf16<<<gridn(n2 * nvec), 256, 0, s>>>(x, OpDst{Wbf.p, wp, x3 ? Wlo.p : nullptr}, nvec, dim, v, n2);
   EA_LAUNCH();
   DArr<bf16> B1((size_t)(nv * 2 * ovp), s), B2((size_t)(nv * 4 * ovp), s), BV1((size_t)(nv * ovp), s),
       BV2((size_t)(nv * ovp), s), B1l, B2l, BV1l, BV2l;
@@ -450,9 +457,9 @@ void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y
                                                OpDst{B2.p + 2 * ovp, 4 * ovp, lo(B2l, 2 * ovp)}, nvec, o, v);
   EA_LAUNCH();
   // tensor-core GEMMs
-  DArr<float> L((size_t)(ov * nvec * vp), s);
-  ladder_tc(s, st, Wbf.p, x3 ? Wlo.p : nullptr, nvec * o, L.p);
-  const long long nvp = pad8(nv);
+  DArr<float> L((size_t)(ov * nvec * lp), s);
+  ladder_tc(s, st, Wbf.p, x3 ? Wlo.p : nullptr, nvec * o, L.p, lp);
+  const long long nvp = rp32(nv);
   DArr<float> T1((size_t)(ov * nvp), s), T2((size_t)(ov * nvp), s), H1((size_t)(ov * nvp), s),
       H23((size_t)(2 * ov * nvp), s);
   TmaMap aT1 = make_tma_3d(st.Kmat_bf.p, 2 * ovp, ov, 1, 2 * ovp, ov * 2 * ovp, 128);
@@ -485,7 +492,7 @@ void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y
   gemm_split(s, aH1, P(aH1l), bV1, P(bV1l), outmap(H1.p, ov), g);
   g.M = (int)(2 * ov);
   gemm_split(s, aH23, P(aH23l), bV2, P(bV2l), outmap(H23.p, 2 * ov), g);
-  combine_ring_ladder<<<gridn(n2 * nvec), 256, 0, s>>>(y, T1.p, T2.p, L.p, nvec, dim, o, v, nvp, vp);
+  combine_ring_ladder<<<gridn(n2 * nvec), 256, 0, s>>>(y, T1.p, T2.p, L.p, nvec, dim, o, v, nvp, lp);
   EA_LAUNCH();
   // 2p1h -> 1p finishing (FP32, CUDA cores) from the tensor-core H tensors
   DArr<float> h1((size_t)(nvec * n2), s), h2((size_t)(nvec * n2), s), h3((size_t)(nvec * n2), s), V((size_t)n2, s),
@@ -507,16 +514,16 @@ void ladder_only(cudaStream_t s, State& st, int nvec, const double* x, float* ou
   const long long ov = (long long)o * v, n2 = ov * v;
   if (!mixed) fail(EAADC_ERR_ARG, "ladder_only: tensor-core path only");
   prepare_mixed(s, st, st.x3_ready);
-  const long long vp = pad8(v);
-  DArr<bf16> Wbf((size_t)(ov * nvec * vp), s);
-  pack_w_bf16<<<gridn(n2 * nvec), 256, 0, s>>>(x, OpDst{Wbf.p, vp, nullptr}, nvec, st.dim, v, n2);
+  const long long wp = rp64(v), lp = rp32(v);
+  DArr<bf16> Wbf((size_t)(ov * nvec * wp), s);
+  pack_w_bf16<<<gridn(n2 * nvec), 256, 0, s>>>(x, OpDst{Wbf.p, wp, nullptr}, nvec, st.dim, v, n2);
   EA_LAUNCH();
-  if (vp == v) {
-    ladder_tc(s, st, Wbf.p, nullptr, nvec * o, out);
+  if (v % 4 == 0) {  // rows of the caller's buffer are whole 16-byte units: write in place
+    ladder_tc(s, st, Wbf.p, nullptr, nvec * o, out, v);
   } else {
-    DArr<float> L((size_t)(ov * nvec * vp), s);
-    ladder_tc(s, st, Wbf.p, nullptr, nvec * o, L.p);
-    compact_f32<<<gridn(n2 * nvec), 256, 0, s>>>(L.p, vp, out, ov * nvec, v);
+    DArr<float> L((size_t)(ov * nvec * lp), s);
+    ladder_tc(s, st, Wbf.p, nullptr, nvec * o, L.p, lp);
+    compact_f32<<<gridn(n2 * nvec), 256, 0, s>>>(L.p, lp, out, ov * nvec, v);
     EA_LAUNCH();
   }
 }

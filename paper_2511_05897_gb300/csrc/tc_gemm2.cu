@@ -48,6 +48,7 @@ TmaMap make_tma_out4d(const void* base, int elem_bytes, long long cols, long lon
 }
 
 int pick_bn(int N) {
+  if (N <= 256) return std::max(32, (N + 15) / 16 * 16);
   int best = 256;
   long long bestw = -1;
   for (int bn = 256; bn >= 128; bn -= 32) {
@@ -57,21 +58,34 @@ int pick_bn(int N) {
   return best;
 }
 
-void tc_gemm2(cudaStream_t s, const TmaMap& A, const TmaMap& B, const TmaMap& C, const tc2::Args& a) {
-  if (a.M <= 0 || a.N <= 0 || a.nz <= 0) return;
-  if (a.BN < 32 || a.BN > 256 || a.BN % 32) fail(EAADC_ERR_ARG, "tc_gemm2: BN must be a multiple of 32 in [32, 256]");
-  if (a.nzlo < 1 || a.nz % a.nzlo) fail(EAADC_ERR_ARG, "tc_gemm2: bad batch split");
-  static bool attr = false;
+namespace {
+template <int kS, int kEB>
+void launch_variant(cudaStream_t s, const TmaMap& A, const TmaMap& B, const TmaMap& C, const tc2::Args& a, int grid) {
+  static bool attr = false;  // opt in to the largest shared-memory size once per variant
   if (!attr) {
-    EA_CK(cudaFuncSetAttribute(tc2::gemm_persistent<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)tc2::smem_bytes(256)));
+    EA_CK(cudaFuncSetAttribute(tc2::gemm_persistent<kS, kEB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tc2::smem_bytes(256, kS, kEB)));
     attr = true;
   }
+  tc2::gemm_persistent<kS, kEB><<<grid, tc2::kThreads, tc2::smem_bytes(a.BN, kS, kEB), s>>>(A.map, B.map, C.map, a);
+  EA_LAUNCH();
+}
+}  // namespace
+
+void tc_gemm2(cudaStream_t s, const TmaMap& A, const TmaMap& B, const TmaMap& C, const tc2::Args& a) {
+  if (a.M <= 0 || a.N <= 0 || a.nz <= 0) return;
+  // BN: an MMA width (multiple of 16, <= 256); the epilogue writes 32-column
+  // chunks, so a width that is not a multiple of 32 needs a single column tile
+  // whose last chunk runs past N (clipped by the output map).
+  if (a.BN < 32 || a.BN > 256 || a.BN % 16 || (a.BN % 32 && (a.N > a.BN || a.c_col0)))
+    fail(EAADC_ERR_ARG, "tc_gemm2: bad tile width");
+  if (a.nzlo < 1 || a.nz % a.nzlo) fail(EAADC_ERR_ARG, "tc_gemm2: bad batch split");
   const long long tiles = (long long)((a.M + tc2::kBM - 1) / tc2::kBM) * ((a.N + a.BN - 1) / a.BN) * a.nz;
   if (tiles > (1LL << 31) - 1) fail(EAADC_ERR_ARG, "tc_gemm2: too many tiles");
   const int grid = (int)std::min<long long>(tiles, sm_count());
-  tc2::gemm_persistent<0><<<grid, tc2::kThreads, tc2::smem_bytes(a.BN), s>>>(A.map, B.map, C.map, a);
-  EA_LAUNCH();
+  const int nk = (a.K + tc2::kBK - 1) / tc2::kBK;
+  if (nk >= 8) launch_variant<4, 2>(s, A, B, C, a, grid);  // long K: bytes in flight
+  else launch_variant<3, 4>(s, A, B, C, a, grid);          // short K: epilogue depth
 }
 
 }  // namespace ea

@@ -1,11 +1,15 @@
 // Persistent warp-specialised BF16 GEMM on tcgen05 (sm_103a):
 //   C[z][m][n] (+)= alpha * sum_k A[z][m][k] * B[z][n][k]
 // One CTA per SM loops over 128 x BN output tiles.  Warp 0 issues TMA loads
-// into a 3-stage shared-memory ring, warp 1 issues tcgen05.mma into one of two
-// TMEM accumulators, warps 2-5 drain the other accumulator (tcgen05.ld),
-// stage 32 x 32 sub-tiles in swizzled shared memory and write them with TMA
-// bulk stores (or TMA reduce-adds when accumulating into C), so the epilogue
-// of one tile overlaps the main loop of the next.
+// into a kS-stage shared-memory ring, warp 1 issues tcgen05.mma into one of two
+// TMEM accumulators, warps 2-5 drain the other accumulator (tcgen05.ld, the
+// next 32 columns loaded while the current ones are written out), stage
+// 32 x 32 sub-tiles in kEB swizzled shared-memory buffers per warp and write
+// them with TMA bulk stores (or TMA reduce-adds when accumulating into C), so
+// the epilogue of one tile overlaps the main loop of the next.  Two shapes:
+// long K wants more bytes in flight (4 stages, 2 staging buffers), short K
+// (few k-blocks per tile, many tiles) wants a deeper epilogue (3 and 4).
+// In the last k-block only the MMAs that touch real K columns are issued.
 //
 // Batch index z = zhi * nzlo + zlo.  Each operand's third TMA coordinate is
 // chosen by a selector (none / zlo / zhi / z) plus an offset; the output map is
@@ -23,7 +27,7 @@ using namespace ea::tc;
 enum ZSel : int { Z_NONE = 0, Z_LO = 1, Z_HI = 2, Z_ALL = 3 };
 
 struct Args {
-  int M, N, K, BN;     // BN: tile width, multiple of 32, <= 256
+  int M, N, K, BN;     // BN: tile width <= 256, multiple of 32 (or of 16 when N <= BN)
   int nzlo, nz;        // batch: z in [0, nz), zlo = z % nzlo, zhi = z / nzlo
   int a_sel, b_sel, a_z0, b_z0;
   int a_row0, b_row0, a_k0, b_k0;
@@ -34,12 +38,12 @@ struct Args {
   int* err;
 };
 
-constexpr int kBM = 128, kBK = 64, kStages = 3, kEpiWarps = 4;
+constexpr int kBM = 128, kBK = 64, kEpiWarps = 4;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kStageA = kBM * kBK * 2;
 
-__host__ __device__ constexpr size_t smem_bytes(int BN) {
-  return 1024 + (size_t)kStages * (kStageA + (size_t)BN * kBK * 2) + (size_t)kEpiWarps * 2 * 4096 + 256;
+__host__ __device__ constexpr size_t smem_bytes(int BN, int stages, int ebufs) {
+  return 1024 + (size_t)stages * (kStageA + (size_t)BN * kBK * 2) + (size_t)kEpiWarps * ebufs * 4096 + 256;
 }
 
 __device__ __forceinline__ int zsel(int sel, int z0, int zlo, int zhi, int z) {
@@ -66,21 +70,31 @@ __device__ __forceinline__ void tma_reduce_add_4d(const CUtensorMap* map, const 
 }
 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory"); }
+
+// Registers written by an asynchronous tcgen05.ld are valid only after
+// tcgen05.wait::ld; this empty asm redefines them after the wait so that no
+// use can be scheduled above it.
+__device__ __forceinline__ void reg_fence(uint32_t (&r)[32]) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) asm volatile("" : "+r"(r[i]));
+}
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
-template <int kVariant = 0>
+template <int kS, int kEB>  // pipeline stages, epilogue staging buffers per warp
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_persistent(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                     const __grid_constant__ CUtensorMap mapC, Args g) {
+  constexpr int kStages = kS;
   extern __shared__ uint8_t smem_raw[];
   const int BN = g.BN;
   const uint32_t stageB = (uint32_t)BN * kBK * 2;
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = base;
   uint8_t* sB = sA + kStages * kStageA;
-  uint8_t* sE = sB + kStages * stageB;  // epilogue staging: kEpiWarps x 2 x 4096 B (1024-aligned)
-  uint64_t* full = (uint64_t*)(sE + kEpiWarps * 2 * 4096);
+  uint8_t* sE = sB + kStages * stageB;  // epilogue staging: kEpiWarps x kEB x 4096 B (1024-aligned)
+  uint64_t* full = (uint64_t*)(sE + kEpiWarps * kEB * 4096);
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;
   uint64_t* acc_empty = acc_full + 2;
@@ -154,8 +168,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint64_t ad = smem_desc_sw128(sA + s * kStageA);
           const uint64_t bd = smem_desc_sw128(sB + s * stageB);
+          const int nmma = (min(kBK, g.K - kb * kBK) + 15) >> 4;  // past K the tile holds zeros
 #pragma unroll
-          for (int j = 0; j < kBK / 16; ++j) mma_bf16(dt, ad + 2 * j, bd + 2 * j, idesc, (kb | j) ? 1u : 0u);
+          for (int j = 0; j < kBK / 16; ++j)
+            if (j < nmma) mma_bf16(dt, ad + 2 * j, bd + 2 * j, idesc, (kb | j) ? 1u : 0u);
           mma_commit(&empty[s]);
         }
         mma_commit(&acc_full[buf]);
@@ -168,9 +184,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // --------------------------------------------------------- epilogue
     const int ew = warp - 2;          // 0..3
     const int q = warp & 3;           // TMEM lane quarter this warp may access
-    uint8_t* stg = sE + ew * 2 * 4096;
+    uint8_t* stg = sE + ew * kEB * 4096;
     int tcount = 0, sbuf = 0;
-    const int ccols = 32;              // columns per staged chunk
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tcount) {
       const int buf = tcount & 1;
       const uint32_t aph = (tcount >> 1) & 1;
@@ -181,13 +196,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int mt = rem / tn, nt = rem % tn;
       const int zlo = z % g.nzlo, zhi = z / g.nzlo;
       const int row0 = g.c_row0 + mt * kBM + q * 32;
-      for (int c0 = 0; c0 < BN; c0 += ccols) {
-        uint32_t r[32];
-        tmem_ld_32x32b_x32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + c0), r);
-        tmem_ld_wait();
+      const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
+      const bool rows_in = mt * kBM + q * 32 < g.M;
+      // one 32 x 32 chunk: registers -> swizzled staging buffer -> TMA store
+      auto drain = [&](uint32_t(&r)[32], int c0) {
         uint8_t* st = stg + sbuf * 4096;
-        // the staging buffer may still be read by the bulk store issued two chunks ago
-        if (lane == 0) bulk_wait_read1();
+        // the buffer may still be read by the bulk store issued kEB chunks ago
+        if (lane == 0) bulk_wait_read<kEB - 1>();
         __syncwarp();
         if (!g.out_bf16) {
           // row = lane, 128-byte rows, 16-byte chunk j at (j ^ (row & 7)) (128-byte swizzle)
@@ -217,13 +232,27 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) {
           const int col = g.c_col0 + nt * BN + c0;
-          if (nt * BN + c0 < g.N && mt * kBM + q * 32 < g.M) {
+          if (nt * BN + c0 < g.N && rows_in) {
             if (g.reduce) tma_reduce_add_4d(&mapC, st, col, zlo, row0, zhi);
             else tma_store_4d(&mapC, st, col, zlo, row0, zhi);
           }
           bulk_commit();
         }
-        sbuf ^= 1;
+        sbuf = sbuf + 1 == kEB ? 0 : sbuf + 1;
+      };
+      uint32_t ra[32], rb[32];
+      tmem_ld_32x32b_x32(taddr, ra);
+      for (int c0 = 0; c0 < BN; c0 += 64) {
+        tmem_ld_wait();
+        reg_fence(ra);
+        if (c0 + 32 < BN) tmem_ld_32x32b_x32(taddr + (uint32_t)(c0 + 32), rb);
+        drain(ra, c0);
+        if (c0 + 32 < BN) {
+          tmem_ld_wait();
+          reg_fence(rb);
+          if (c0 + 64 < BN) tmem_ld_32x32b_x32(taddr + (uint32_t)(c0 + 64), ra);
+          drain(rb, c0 + 32);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -248,7 +277,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 TmaMap make_tma_out4d(const void* base, int elem_bytes, long long cols, long long nzlo, long long rows, long long nzhi,
                       long long pitch_zlo, long long pitch_row, long long pitch_zhi);
 void tc_gemm2(cudaStream_t s, const TmaMap& A, const TmaMap& B, const TmaMap& C, const tc2::Args& a);
-// Tile width (multiple of 32 in [128, 256]) with the least padding of N.
+// Tile width with the least padding of N: N rounded up to 16 when N <= 256
+// (a single column tile), else a multiple of 32 in [128, 256].
 int pick_bn(int N);
 
 }  // namespace ea

@@ -103,18 +103,18 @@ def test_ladder_noalloc_rejects_what_does_not_fit(E):
         E.eaadc_build_canonical(ctx, 3, 1.0)
         dim = E.eaadc_state_info(ctx, 0)[2]
         o, v = pr["o"], pr["v"]
-        x = torch.zeros((11, dim), dtype=torch.float64, device="cuda:0")
-        out = torch.zeros((11, o, v, v), dtype=torch.float32, device="cuda:0")
+        x = torch.zeros((9, dim), dtype=torch.float64, device="cuda:0")
+        out = torch.zeros((9, o, v, v), dtype=torch.float32, device="cuda:0")
         stream = torch.cuda.current_stream().cuda_stream
         with pytest.raises(E.EaadcError) as err:
             E.eaadc_ladder_noalloc(ctx, 0, 1, x.data_ptr(), out.data_ptr(), stream)
         assert err.value.status == E.EAADC_ERR_STATE and "BF16 operands" in str(err.value)
         E.eaadc_ladder(ctx, 0, 1, x.data_ptr(), out.data_ptr(), stream)  # makes the BF16 operands
         with pytest.raises(E.EaadcError) as err:
-            E.eaadc_ladder_noalloc(ctx, 0, 11, x.data_ptr(), out.data_ptr(), stream)
+            E.eaadc_ladder_noalloc(ctx, 0, 9, x.data_ptr(), out.data_ptr(), stream)
         assert err.value.status == E.EAADC_ERR_ARG and "fixed limit" in str(err.value)
-        E.eaadc_ladder_noalloc(ctx, 0, 10, x.data_ptr(), out.data_ptr(), stream)  # 10 vectors fit
+        E.eaadc_ladder_noalloc(ctx, 0, 8, x.data_ptr(), out.data_ptr(), stream)  # 8 vectors fit
         torch.cuda.synchronize()
-        assert not out[:10].any()
+        assert not out[:8].any()
     finally:
         E.eaadc_destroy(ctx)
