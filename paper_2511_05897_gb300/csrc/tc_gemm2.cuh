@@ -9,7 +9,8 @@
 // the epilogue of one tile overlaps the main loop of the next.  Two shapes:
 // long K wants more bytes in flight (4 stages, 2 staging buffers), short K
 // (few k-blocks per tile, many tiles) wants a deeper epilogue (3 and 4).
-// In the last k-block only the MMAs that touch real K columns are issued.
+// In the last k-block only the MMAs that touch real K columns are issued;
+// each CTA starts its K loop at a different block (the sum is order-free).
 //
 // Batch index z = zhi * nzlo + zlo.  Each operand's third TMA coordinate is
 // chosen by a selector (none / zlo / zhi / z) plus an offset; the output map is
@@ -106,6 +107,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int tm = (g.M + kBM - 1) / kBM, tn = (g.N + BN - 1) / BN;
   const int ntiles = tm * tn * g.nz;
   const int nk = (g.K + kBK - 1) / kBK;
+  // Each CTA walks K from its own starting block, so that CTAs sharing an
+  // operand tile do not all request the same lines from L2 at the same time.
+  const int krot = (int)(((long long)blockIdx.x * nk) / gridDim.x) % nk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -132,7 +136,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int mt = rem / tn, nt = rem % tn;
         const int zlo = z % g.nzlo, zhi = z / g.nzlo;
         const int az = zsel(g.a_sel, g.a_z0, zlo, zhi, z), bz = zsel(g.b_sel, g.b_z0, zlo, zhi, z);
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        for (int ki = 0; ki < nk; ++ki, ++it) {
+          const int kb = ki + krot < nk ? ki + krot : ki + krot - nk;
           const int s = it % kStages;
           const uint32_t ph = (it / kStages) & 1;
           if (it >= kStages && !mbar_wait(&empty[s], ph ^ 1, abort_flag, g.err, 201)) break;
@@ -161,7 +166,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t dt = tmem + (uint32_t)(buf * 256);
         bool ok = true;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
+        for (int ki = 0; ki < nk; ++ki, ++it) {
+          const int kb = ki + krot < nk ? ki + krot : ki + krot - nk;
           const int s = it % kStages;
           const uint32_t ph = (it / kStages) & 1;
           if (!mbar_wait(&full[s], ph, abort_flag, g.err, 203)) { ok = false; break; }
@@ -171,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int nmma = (min(kBK, g.K - kb * kBK) + 15) >> 4;  // past K the tile holds zeros
 #pragma unroll
           for (int j = 0; j < kBK / 16; ++j)
-            if (j < nmma) mma_bf16(dt, ad + 2 * j, bd + 2 * j, idesc, (kb | j) ? 1u : 0u);
+            if (j < nmma) mma_bf16(dt, ad + 2 * j, bd + 2 * j, idesc, (ki | j) ? 1u : 0u);
           mma_commit(&empty[s]);
         }
         mma_commit(&acc_full[buf]);
