@@ -171,8 +171,53 @@ eaadc_status eaadc_ladder_noalloc(eaadc_ctx* ctx, int state, int nvec, const dou
  * 1p part, e_b + e_c - e_k for the 2p1h part. */
 eaadc_status eaadc_diagonal(eaadc_ctx* ctx, int state, double* diag_host);
 
+/* Per-state truncated spaces (Sec. II.C-E; the algorithm of Sec. III),
+ * replacing any states built before.  Solves the canonical EA-ADC(2) problem
+ * for its nstates lowest roots (FP64 Davidson with can_opts, or tol 1e-8,
+ * maxit 300, max_sub 40 when NULL); root k defines state k:
+ *   D^SS(k) = D^MP2 + D^EA(k) (Eq. 17; D^EA from the zeroth-order ISR of the
+ *   root: y_a y_b + sum_kc (w_kac w_kbc + w_kca w_kcb), spin-summed),
+ *   eigenvectors with occupation > fno_thresh[k] kept (Eq. 9-11; < 0 keeps
+ *   all), semicanonicalised (Eq. 12-14); the DF factor transformed to that
+ *   basis; W = J J^T over its vv block (Eq. 27-28), eigenvectors with
+ *   eigenvalue >= naf_thresh[k] kept (< 0 keeps all), J~ = N~^T J (Eq. 29)
+ *   for the oo, ov and vv blocks; then the ADC(adc_order) intermediates of
+ *   the truncated problem, with x3 scaling M^(3) as in eaadc_build_canonical.
+ * All eigenproblems run on the device (eaadc_eigh_sym).  eaadc_state_info
+ * gives each state's v' and naux'; eaadc_davidson then solves every state and
+ * records its target root: the Ritz vector whose 1p part overlaps most with
+ * the canonical root's 1p part carried into the FNO basis (ties: lower root).
+ *  fno_thresh, naf_thresh : host [nstates]
+ * Errors: EAADC_ERR_ARG for a threshold that keeps nothing, EAADC_ERR_NOCONV
+ * if the canonical roots do not converge. */
+eaadc_status eaadc_build_states(eaadc_ctx* ctx, int nstates, const double* fno_thresh,
+                                const double* naf_thresh, int adc_order, double x3,
+                                const eaadc_davidson_opts* can_opts);
+
+/* Eq. 30 for every state from eaadc_build_states, after eaadc_davidson:
+ *   omega_corr = omega^(3)_FNO + omega^(2)_canonical - omega^(2)_FNO,
+ * omega^(3)_FNO the target root of the last eaadc_davidson, omega^(2)_FNO the
+ * target root of EA-ADC(2) solved here in the same truncated space (FP64
+ * Davidson with opts, defaults as for eaadc_build_states; as many roots as the
+ * last eaadc_davidson).  Attachment energies in hartree (EA = -omega).
+ * Each output is host [nstates] and may be NULL. */
+eaadc_status eaadc_ea_energies(eaadc_ctx* ctx, const eaadc_davidson_opts* opts, double* omega_uncorr,
+                               double* omega_corr, double* omega2_can, double* omega2_fno);
+
+/* Dense FP64 symmetric eigensolver used for the FNO and NAF bases (Eq. 9, 13,
+ * 28): a_dev [n][n] device, read only (its symmetric part is used);
+ * eigenvalues ascending into w_dev [n], eigenvectors as the columns of v_dev
+ * [n][n] (row-major).  Two-sided block Jacobi (32 x 32 blocks, pair
+ * sub-problems solved in shared memory); n <= 96 in one CTA.  Works on the
+ * given device and stream; allocates its own temporary device memory. */
+eaadc_status eaadc_eigh_sym(int n, const double* a_dev, double* w_dev, double* v_dev, int device,
+                            void* stream);
+
 /* Copy the 1p/1p block M_ab of a state to host [v'][v']. */
 eaadc_status eaadc_get_m11(eaadc_ctx* ctx, int state, double* m11_host);
+
+/* Number of states currently built (0 for ctx == NULL). */
+int eaadc_num_states(const eaadc_ctx* ctx);
 
 /* Lowest nroots roots of every built state by Davidson.
  *  omega   : host [nstates][nroots] Ritz values (hartree)

@@ -28,7 +28,7 @@ EXPORTED = (
     "eaadc_version", "eaadc_init", "eaadc_build_canonical", "eaadc_state_info", "eaadc_sigma",
     "eaadc_sigma_host", "eaadc_diagonal", "eaadc_get_m11", "eaadc_davidson", "eaadc_get_eigvecs",
     "eaadc_destroy", "eaadc_last_error", "eaadc_ladder", "eaadc_kernel_launches",
-    "eaadc_ladder_noalloc",
+    "eaadc_ladder_noalloc", "eaadc_build_states", "eaadc_ea_energies", "eaadc_eigh_sym", "eaadc_num_states",
 )
 
 
@@ -63,6 +63,11 @@ def lib():
         L.eaadc_diagonal.argtypes = [vp, C.c_int, dp]
         L.eaadc_ladder.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
         L.eaadc_ladder_noalloc.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
+        L.eaadc_build_states.argtypes = [vp, C.c_int, dp, dp, C.c_int, C.c_double, C.POINTER(DavidsonOpts)]
+        L.eaadc_ea_energies.argtypes = [vp, C.POINTER(DavidsonOpts), dp, dp, dp, dp]
+        L.eaadc_eigh_sym.argtypes = [C.c_int, vp, vp, vp, C.c_int, vp]
+        L.eaadc_num_states.argtypes = [vp]
+        L.eaadc_num_states.restype = C.c_int
         L.eaadc_get_m11.argtypes = [vp, C.c_int, dp]
         L.eaadc_davidson.argtypes = [vp, C.c_int, C.POINTER(DavidsonOpts), dp, dp, ip]
         L.eaadc_get_eigvecs.argtypes = [vp, C.c_int, dp]
@@ -71,7 +76,8 @@ def lib():
         L.eaadc_last_error.argtypes = [vp]
         L.eaadc_last_error.restype = C.c_char_p
         for name in EXPORTED:
-            if name not in ("eaadc_version", "eaadc_destroy", "eaadc_last_error", "eaadc_kernel_launches"):
+            if name not in ("eaadc_version", "eaadc_destroy", "eaadc_last_error", "eaadc_kernel_launches",
+                            "eaadc_num_states"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -146,6 +152,37 @@ def eaadc_ladder_noalloc(ctx, state, nvec, x_ptr, out_ptr, stream=None):
     _check(ctx, lib().eaadc_ladder_noalloc(ctx, state, nvec, C.c_void_p(x_ptr), C.c_void_p(out_ptr), stream))
 
 
+def eaadc_build_states(ctx, nstates, fno_thresh, naf_thresh, adc_order=3, x3=1.0, can_opts=None):
+    """Per-state FNO/NAF truncated spaces from the nstates lowest canonical
+    EA-ADC(2) roots; thresholds are scalars or per-state sequences (< 0 keeps all).
+    can_opts: dict of Davidson options for the canonical ADC(2) solve, or None."""
+    f = np.ascontiguousarray(np.broadcast_to(np.asarray(fno_thresh, dtype=np.float64), (nstates,)))
+    n = np.ascontiguousarray(np.broadcast_to(np.asarray(naf_thresh, dtype=np.float64), (nstates,)))
+    o = C.byref(DavidsonOpts(**_opts(can_opts))) if can_opts is not None else None
+    _check(ctx, lib().eaadc_build_states(ctx, nstates, _dp(f), _dp(n), adc_order, x3, o))
+
+
+def eaadc_ea_energies(ctx, opts=None):
+    """Eq. 30 per state: dict of omega_uncorr, omega_corr, omega2_can, omega2_fno (hartree)."""
+    nstates = max(eaadc_num_states(ctx), 1)
+    out = {k: np.zeros(nstates) for k in ("omega_uncorr", "omega_corr", "omega2_can", "omega2_fno")}
+    o = C.byref(DavidsonOpts(**_opts(opts))) if opts is not None else None
+    _check(ctx, lib().eaadc_ea_energies(ctx, o, _dp(out["omega_uncorr"]), _dp(out["omega_corr"]),
+                                        _dp(out["omega2_can"]), _dp(out["omega2_fno"])))
+    return out
+
+
+def eaadc_eigh_sym(n, a_ptr, w_ptr, v_ptr, device=0, stream=None):
+    """Device pointers: a [n][n] float64 (read), w [n], v [n][n] (eigenvectors as columns)."""
+    _check(None, lib().eaadc_eigh_sym(n, C.c_void_p(a_ptr), C.c_void_p(w_ptr), C.c_void_p(v_ptr), device, stream))
+
+
+def _opts(d):
+    base = dict(tol=1e-8, etol=1e-10, maxit=300, max_sub=40, prec=EAADC_FP64, refine=0)
+    base.update(d)
+    return base
+
+
 def eaadc_diagonal(ctx, state=0):
     dim = eaadc_state_info(ctx, state)[2]
     out = np.empty(dim)
@@ -160,13 +197,17 @@ def eaadc_get_m11(ctx, state=0):
     return out
 
 
-def eaadc_davidson(ctx, nroots, nstates=1, tol=1e-6, etol=1e-10, maxit=200, max_sub=40, prec=EAADC_FP64,
-                   refine=1):
+def eaadc_num_states(ctx):
+    return lib().eaadc_num_states(ctx)
+
+
+def eaadc_davidson(ctx, nroots, tol=1e-6, etol=1e-10, maxit=200, max_sub=40, prec=EAADC_FP64, refine=1):
     """Returns (omega[nstates, nroots], resnorm[nstates, nroots], iters[nstates], status)."""
+    nstates = eaadc_num_states(ctx)
     opts = DavidsonOpts(tol, etol, maxit, max_sub, prec, refine)
-    om = np.zeros((nstates, nroots))
-    rn = np.zeros((nstates, nroots))
-    it = np.zeros(nstates, dtype=np.int32)
+    om = np.zeros((max(nstates, 1), nroots))
+    rn = np.zeros((max(nstates, 1), nroots))
+    it = np.zeros(max(nstates, 1), dtype=np.int32)
     st = lib().eaadc_davidson(ctx, nroots, C.byref(opts), _dp(om), _dp(rn),
                               it.ctypes.data_as(C.POINTER(C.c_int)))
     if st not in (EAADC_OK, EAADC_ERR_NOCONV):

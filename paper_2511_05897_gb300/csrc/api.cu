@@ -128,6 +128,55 @@ eaadc_status eaadc_build_canonical(eaadc_ctx* ctx, int adc_order, double x3) {
   });
 }
 
+namespace {
+eaadc_davidson_opts inner_opts(const eaadc_davidson_opts* o) {
+  if (o) {
+    if (!(o->tol > 0) || o->maxit < 1) ea::fail(EAADC_ERR_ARG, "bad Davidson options");
+    if (o->prec != EAADC_FP64 && o->prec != EAADC_MIXED_BF16 && o->prec != EAADC_MIXED_BF16X3)
+      ea::fail(EAADC_ERR_ARG, "unknown precision");
+    return *o;
+  }
+  eaadc_davidson_opts d;
+  d.tol = 1e-8; d.etol = 1e-10; d.maxit = 300; d.max_sub = 40; d.prec = EAADC_FP64; d.refine = 0;
+  return d;
+}
+}  // namespace
+
+eaadc_status eaadc_build_states(eaadc_ctx* ctx, int nstates, const double* fno_thresh, const double* naf_thresh,
+                                int adc_order, double x3, const eaadc_davidson_opts* can_opts) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    if (nstates < 1 || !fno_thresh || !naf_thresh) ea::fail(EAADC_ERR_ARG, "bad state count or NULL thresholds");
+    if (adc_order != 2 && adc_order != 3) ea::fail(EAADC_ERR_ARG, "adc_order must be 2 or 3");
+    if (!std::isfinite(x3)) ea::fail(EAADC_ERR_ARG, "x3 must be finite");
+    if (!all_finite(fno_thresh, nstates) || !all_finite(naf_thresh, nstates))
+      ea::fail(EAADC_ERR_NONFINITE, "non-finite threshold");
+    set_device(ctx);
+    ea::build_fno_states(ctx, nstates, fno_thresh, naf_thresh, adc_order, x3, inner_opts(can_opts));
+  });
+}
+
+eaadc_status eaadc_ea_energies(eaadc_ctx* ctx, const eaadc_davidson_opts* opts, double* omega_uncorr,
+                               double* omega_corr, double* omega2_can, double* omega2_fno) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    if (ctx->states.empty()) ea::fail(EAADC_ERR_STATE, "no states built");
+    set_device(ctx);
+    ea::ea_energies(ctx, inner_opts(opts), omega_uncorr, omega_corr, omega2_can, omega2_fno);
+  });
+}
+
+eaadc_status eaadc_eigh_sym(int n, const double* a_dev, double* w_dev, double* v_dev, int device, void* stream) {
+  return guarded(nullptr, [&] {
+    if (n < 1 || !a_dev || !w_dev || !v_dev) ea::fail(EAADC_ERR_ARG, "bad size or NULL pointer");
+    int ndev = 0;
+    EA_CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) ea::fail(EAADC_ERR_ARG, "device index out of range");
+    EA_CK(cudaSetDevice(device));
+    ea::eigh_sym((cudaStream_t)stream, n, a_dev, w_dev, v_dev);
+  });
+}
+
 eaadc_status eaadc_state_info(const eaadc_ctx* ctx, int state, int* vprime, int* nauxprime, long long* dim) {
   if (!ctx) return EAADC_ERR_ARG;
   if (state < 0 || state >= (int)ctx->states.size()) return EAADC_ERR_ARG;
@@ -211,6 +260,8 @@ eaadc_status eaadc_get_m11(eaadc_ctx* ctx, int state, double* m11_host) {
     EA_CK(cudaStreamSynchronize(ctx->stream));
   });
 }
+
+int eaadc_num_states(const eaadc_ctx* ctx) { return ctx ? (int)ctx->states.size() : 0; }
 
 eaadc_status eaadc_davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts* opts, double* omega,
                             double* resnorm, int* iters) {

@@ -319,47 +319,59 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
   return conv;
 }
 
+bool davidson_state(cudaStream_t s, State& st, int nroots, const eaadc_davidson_opts& opt, double* omega,
+                    double* resnorm, int* iters) {
+  const long long n = st.dim;
+  int k = (int)std::min<long long>(nroots, n);
+  int mmax = (int)std::min<long long>(std::min(opt.max_sub, 96), n);
+  if (mmax < 2 * k) mmax = (int)std::min<long long>(2 * k, n);
+  if (mmax > 96) fail(EAADC_ERR_ARG, "davidson: subspace would exceed 96 vectors");
+  DArr<double> V((size_t)mmax * n, s), S((size_t)mmax * n, s);
+  st.evecs.alloc((size_t)k * n, s);
+  st.nvecs = k;
+  // guesses on the k lowest diagonal entries
+  DArr<int> idx((size_t)k, s);
+  int npart = std::min(256, (int)std::max<long long>(1, (n + 255) / 256));
+  DArr<double> pv((size_t)npart, s);
+  DArr<long long> pi((size_t)npart, s);
+  for (int r = 0; r < k; ++r) {
+    argmin_partial<<<npart, 256, 0, s>>>(st.diag.p, n, idx.p, r, pv.p, pi.p);
+    EA_LAUNCH();
+    argmin_final<<<1, 1, 0, s>>>(pv.p, pi.p, npart, idx.p + r);
+    EA_LAUNCH();
+  }
+  set_units<<<gridn(n * k), 256, 0, s>>>(V.p, n, idx.p, k);
+  EA_LAUNCH();
+  std::vector<double> theta, rn;
+  int it = 0;
+  const bool refine = opt.prec != EAADC_FP64 && opt.refine;
+  bool conv = davidson_phase(s, st, k, opt.prec, opt, V, S, mmax, k, theta, rn, it, st.evecs, refine);
+  if (refine) {
+    // FP64 refinement from the mixed-precision Ritz vectors
+    EA_CK(cudaMemcpyAsync(V.p, st.evecs.p, sizeof(double) * k * n, cudaMemcpyDeviceToDevice, s));
+    conv = davidson_phase(s, st, k, EAADC_FP64, opt, V, S, mmax, k, theta, rn, it, st.evecs, false);
+  }
+  for (int r = 0; r < k; ++r) {
+    omega[r] = theta[r];
+    if (resnorm) resnorm[r] = rn[r];
+  }
+  for (int r = k; r < nroots; ++r) {
+    omega[r] = NAN;
+    if (resnorm) resnorm[r] = NAN;
+  }
+  st.omega.assign(theta.begin(), theta.begin() + k);
+  if (iters) *iters = it;
+  return conv;
+}
+
 void davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts& opt, double* omega, double* resnorm, int* iters,
               bool* converged) {
-  cudaStream_t s = ctx->stream;
   *converged = true;
   for (size_t si = 0; si < ctx->states.size(); ++si) {
     State& st = *ctx->states[si];
-    const long long n = st.dim;
-    int k = (int)std::min<long long>(nroots, n);
-    int mmax = (int)std::min<long long>(std::min(opt.max_sub, 96), n);
-    if (mmax < 2 * k) mmax = (int)std::min<long long>(2 * k, n);
-    if (mmax > 96) fail(EAADC_ERR_ARG, "davidson: subspace would exceed 96 vectors");
-    DArr<double> V((size_t)mmax * n, s), S((size_t)mmax * n, s);
-    st.evecs.alloc((size_t)k * n, s);
-    st.nvecs = k;
-    // guesses on the k lowest diagonal entries
-    DArr<int> idx((size_t)k, s);
-    int npart = std::min(256, (int)std::max<long long>(1, (n + 255) / 256));
-    DArr<double> pv((size_t)npart, s);
-    DArr<long long> pi((size_t)npart, s);
-    for (int r = 0; r < k; ++r) {
-      argmin_partial<<<npart, 256, 0, s>>>(st.diag.p, n, idx.p, r, pv.p, pi.p);
-      EA_LAUNCH();
-      argmin_final<<<1, 1, 0, s>>>(pv.p, pi.p, npart, idx.p + r);
-      EA_LAUNCH();
-    }
-    set_units<<<gridn(n * k), 256, 0, s>>>(V.p, n, idx.p, k);
-    EA_LAUNCH();
-    std::vector<double> theta, rn;
-    int it = 0;
-    const bool refine = opt.prec != EAADC_FP64 && opt.refine;
-    bool conv = davidson_phase(s, st, k, opt.prec, opt, V, S, mmax, k, theta, rn, it, st.evecs, refine);
-    if (refine) {
-      // FP64 refinement from the mixed-precision Ritz vectors
-      EA_CK(cudaMemcpyAsync(V.p, st.evecs.p, sizeof(double) * k * n, cudaMemcpyDeviceToDevice, s));
-      conv = davidson_phase(s, st, k, EAADC_FP64, opt, V, S, mmax, k, theta, rn, it, st.evecs, false);
-    }
-    for (int r = 0; r < k; ++r) {
-      omega[si * nroots + r] = theta[r];
-      if (resnorm) resnorm[si * nroots + r] = rn[r];
-    }
-    if (iters) iters[si] = it;
+    const bool conv = davidson_state(ctx->stream, st, nroots, opt, omega + si * nroots,
+                                     resnorm ? resnorm + si * nroots : nullptr, iters ? iters + si : nullptr);
+    if (st.ref1p.p) pick_target(ctx->stream, st);
     *converged &= conv;
   }
 }

@@ -153,6 +153,12 @@ struct State {
   DArr<float> Boo32, Bov32, Bvv32, tau32;     // FP32 copies for the DF coupling pieces
   DArr<bf16> Bvv_lo, Bb_lo, Kmat_lo, Jmat_lo, tauA_lo, tm2A_lo;  // low parts (split-BF16 mode)
   bool x3_ready = false;
+  // per-state FNO/NAF data (states from eaadc_build_states)
+  DArr<double> ref1p;                          // canonical ADC(2) root's 1p part in this basis [v']
+  double omega2_can = 0.0;                     // that canonical ADC(2) root
+  int vfull = 0, nauxfull = 0;                 // untruncated sizes
+  std::vector<double> omega;                   // roots of the last Davidson
+  int target = -1;                             // index of the target root
   long long bvv_pitch = 0, bb_pitch = 0;      // row pitches (elements) of Bvv_bf and Bb_bf
   DArr<int> err;                              // device error word of bounded waits
   bool mixed_ready = false;
@@ -196,9 +202,26 @@ void couple_2p1h_to_1p(cudaStream_t s, State& st, const double* V, double* sy, c
                        const double* H1g, const double* H2g, const double* H3g);
 void ladder_only(cudaStream_t s, State& st, int nvec, const double* x, float* out, bool mixed);
 void make_diagonal(cudaStream_t s, State& st);
+// Lowest nroots roots of one state (Ritz vectors into st.evecs, values into
+// st.omega); returns true if converged.
+bool davidson_state(cudaStream_t s, State& st, int nroots, const eaadc_davidson_opts& opt, double* omega,
+                    double* resnorm, int* iters);
+// Target root of an FNO state: largest |overlap| of the 1p part with ref1p.
+void pick_target(cudaStream_t s, State& st);
+// Per-state FNO/NAF truncated states replacing ctx->states (Sec. III) and
+// the Eq. 30 energies of the target roots.
+void build_fno_states(eaadc_ctx* ctx, int nstates, const double* fno_thr, const double* naf_thr, int order, double x3,
+                      const eaadc_davidson_opts& copts);
+void ea_energies(eaadc_ctx* ctx, const eaadc_davidson_opts& opts, double* w_uncorr, double* w_corr, double* w2_can,
+                 double* w2_fno);
 void davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts& opt, double* omega,
               double* resnorm, int* iters, bool* converged);
-// Dense symmetric eigensolver (cyclic Jacobi, one CTA): A [m][m] (destroyed),
-// eigenvalues ascending into w[m], eigenvectors as columns of U [m][m].
-void jacobi_eigh(cudaStream_t s, int m, double* A, double* w, double* U);
+// Dense symmetric eigensolver (cyclic Jacobi, one CTA per matrix, m <= 96):
+// nbatch matrices A [m][m] (read only), eigenvalues ascending into w[m],
+// eigenvectors as columns of U [m][m].
+void jacobi_eigh(cudaStream_t s, int m, double* A, double* w, double* U, int nbatch = 1);
+// Dense symmetric eigensolver of any order n (FP64, two-sided block Jacobi):
+// A [n][n] on the device (read only), eigenvalues ascending into w[n],
+// eigenvectors as columns of V [n][n].
+void eigh_sym(cudaStream_t s, int n, const double* A, double* w, double* V);
 }  // namespace ea

@@ -371,6 +371,10 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int m, double* __restrict_
   __shared__ double red[32];
   __shared__ int stop;
   const int tid = threadIdx.x, nt = blockDim.x;
+  // batch: one matrix per CTA
+  Ag += (size_t)blockIdx.x * m * m;
+  Ug += (size_t)blockIdx.x * m * m;
+  w += (size_t)blockIdx.x * m;
   for (int i = tid; i < m * m; i += nt) {
     A[i] = Ag[i];
     U[i] = (i / m == i % m) ? 1.0 : 0.0;
@@ -463,8 +467,8 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int m, double* __restrict_
 }
 }  // namespace
 
-void jacobi_eigh(cudaStream_t s, int m, double* A, double* w, double* U) {
-  if (m <= 0) return;
+void jacobi_eigh(cudaStream_t s, int m, double* A, double* w, double* U, int nbatch) {
+  if (m <= 0 || nbatch <= 0) return;
   if (m > 96) fail(EAADC_ERR_ARG, "jacobi_eigh: m > 96");
   int n = (m + 1) & ~1;
   size_t smem = sizeof(double) * (2 * (size_t)m * m + n) + sizeof(int) * n;
@@ -473,7 +477,7 @@ void jacobi_eigh(cudaStream_t s, int m, double* A, double* w, double* U) {
     EA_CK(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     attr = true;
   }
-  jacobi_kernel<<<1, 1024, smem, s>>>(m, A, w, U, 60);
+  jacobi_kernel<<<nbatch, 1024, smem, s>>>(m, A, w, U, 60);
   EA_LAUNCH();
 }
 
