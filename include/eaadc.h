@@ -71,6 +71,13 @@ typedef struct {
   int refine;     /* 1: after a mixed-precision solve, FP64 sigma of the Ritz
                      vectors and FP64 Rayleigh-Ritz, then FP64 Davidson
                      iterations until tol is met in FP64 */
+  int precond;    /* 0: diagonal correction r/(theta - D); 1: learned
+                     correction (weights from eaadc_precond_load), falling
+                     back to the diagonal one, for the rest of the solve, for
+                     a root whose residual norm grew after a learned step */
+  int trace;      /* record the Ritz vectors, residuals and Ritz values of the
+                     first `trace` iterations of each state (eaadc_get_trace);
+                     0: none */
 } eaadc_davidson_opts;
 
 /* Library version string (static storage). */
@@ -212,6 +219,64 @@ eaadc_status eaadc_ea_energies(eaadc_ctx* ctx, const eaadc_davidson_opts* opts, 
  * given device and stream; allocates its own temporary device memory. */
 eaadc_status eaadc_eigh_sym(int n, const double* a_dev, double* w_dev, double* v_dev, int device,
                             void* stream);
+
+/* ---------------------------------------------- learned Davidson correction
+ * Not in the paper: a per-element network that adds to the diagonal
+ * correction.  For a root with Ritz value theta and residual r, element I of
+ * the expansion vector is rr_I (1/(theta - D_I) + m_I), rr = r/||r||, D the
+ * diagonal of eaadc_diagonal (|theta - D_I| >= 1e-8), m_I = MLP(f_I):
+ *   h1 = tanh(W1 f + b1), h2 = tanh(W2 h1 + b2), h3 = tanh(W3 h2 + b3),
+ *   m = w4 . h3 + b4   (width 256, FP32 on the device)
+ * with the 16 features f_I (rr_I sqrt(dim), asinh(D_I - theta),
+ * clip(1/(theta - D_I), +-100)/100, eps_k, asinh(eps_b) (1p: asinh(eps_a)),
+ * asinh(eps_c), theta, log10 ||r||, [1p], [2p1h with b = c], 6 zeros).
+ * Weights: EAADC_MLP_PARAMS floats, W1[256][16] b1[256] W2[256][256] b2
+ * W3[256][256] b3 w4[256] b4[1].  Training minimises the mean over vectors of
+ * 1 - cos^2(delta, t), t = (I - y y^T)(y* - y) the exact correction of the
+ * Ritz vector y towards the converged eigenvector y* (sign-aligned). */
+#define EAADC_MLP_FEATURES 16
+#define EAADC_MLP_PARAMS 136193
+
+/* Load (host FP32, bytes = 4 * EAADC_MLP_PARAMS) the network used by
+ * eaadc_davidson when opts.precond = 1; resets the Adam moments. */
+eaadc_status eaadc_precond_load(eaadc_ctx* ctx, const float* weights, size_t bytes);
+/* Copy the current weights to the host. */
+eaadc_status eaadc_precond_get(eaadc_ctx* ctx, float* weights, size_t bytes);
+
+/* Training pairs for nvec Ritz vectors of a state: y_dev, r_dev device
+ * [nvec][dim] FP64 (Ritz vectors, residuals), theta_host [nvec]; ystar_dev
+ * [nvec][dim] the converged eigenvectors of the same roots (or NULL, then
+ * target_dev must be NULL too).  Outputs (device FP32, row = (vector,
+ * element)): feat_dev [nvec*dim][16], rr_dev and base_dev [nvec*dim] (rr and
+ * rr/(theta - D)), target_dev [nvec*dim]. */
+eaadc_status eaadc_precond_pairs(eaadc_ctx* ctx, int state, int nvec, const double* y_dev,
+                                 const double* r_dev, const double* theta_host, const double* ystar_dev,
+                                 float* feat_dev, float* rr_dev, float* base_dev, float* target_dev,
+                                 void* stream);
+
+/* m_dev[i] = MLP(feat_dev[i]) for n rows (device FP32). */
+eaadc_status eaadc_mlp_forward(eaadc_ctx* ctx, long long n, const float* feat_dev, float* m_dev, void* stream);
+
+/* Loss and gradient of a batch of nseg vectors: rows seg_host[j] ..
+ * seg_host[j+1]-1 (seg_host host [nseg+1], seg_host[0] = 0, increasing) of
+ * the device arrays from eaadc_precond_pairs.  loss_host (may be NULL) gets
+ * the mean loss, grad_host (may be NULL) the EAADC_MLP_PARAMS gradient. */
+eaadc_status eaadc_mlp_loss_grad(eaadc_ctx* ctx, int nseg, const int* seg_host, const float* feat_dev,
+                                 const float* rr_dev, const float* base_dev, const float* target_dev,
+                                 double* loss_host, float* grad_host, void* stream);
+
+/* As eaadc_mlp_loss_grad, then one Adam step (beta 0.9/0.999, eps 1e-8) with
+ * learning rate lr on the loaded weights. */
+eaadc_status eaadc_mlp_train_step(eaadc_ctx* ctx, int nseg, const int* seg_host, const float* feat_dev,
+                                  const float* rr_dev, const float* base_dev, const float* target_dev,
+                                  float lr, double* loss_host, void* stream);
+
+/* The trace of the last eaadc_davidson with opts.trace > 0: *niters
+ * iterations of *nroots roots; x_host, r_host [niters][nroots][dim] (Ritz
+ * vectors, residuals), theta_host [niters][nroots].  Pointers may be NULL
+ * (query the sizes first). */
+eaadc_status eaadc_get_trace(eaadc_ctx* ctx, int state, int* niters, int* nroots, double* x_host,
+                             double* r_host, double* theta_host);
 
 /* Copy the 1p/1p block M_ab of a state to host [v'][v']. */
 eaadc_status eaadc_get_m11(eaadc_ctx* ctx, int state, double* m11_host);

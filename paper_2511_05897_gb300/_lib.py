@@ -29,7 +29,11 @@ EXPORTED = (
     "eaadc_sigma_host", "eaadc_diagonal", "eaadc_get_m11", "eaadc_davidson", "eaadc_get_eigvecs",
     "eaadc_destroy", "eaadc_last_error", "eaadc_ladder", "eaadc_kernel_launches",
     "eaadc_ladder_noalloc", "eaadc_build_states", "eaadc_ea_energies", "eaadc_eigh_sym", "eaadc_num_states",
+    "eaadc_precond_load", "eaadc_precond_get", "eaadc_precond_pairs", "eaadc_mlp_forward", "eaadc_mlp_loss_grad",
+    "eaadc_mlp_train_step", "eaadc_get_trace",
 )
+MLP_FEATURES = 16
+MLP_PARAMS = 136193
 
 
 class EaadcError(RuntimeError):
@@ -40,7 +44,7 @@ class EaadcError(RuntimeError):
 
 class DavidsonOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("etol", C.c_double), ("maxit", C.c_int), ("max_sub", C.c_int),
-                ("prec", C.c_int), ("refine", C.c_int)]
+                ("prec", C.c_int), ("refine", C.c_int), ("precond", C.c_int), ("trace", C.c_int)]
 
 
 _lib = None
@@ -67,6 +71,14 @@ def lib():
         L.eaadc_ea_energies.argtypes = [vp, C.POINTER(DavidsonOpts), dp, dp, dp, dp]
         L.eaadc_eigh_sym.argtypes = [C.c_int, vp, vp, vp, C.c_int, vp]
         L.eaadc_num_states.argtypes = [vp]
+        fp = C.POINTER(C.c_float)
+        L.eaadc_precond_load.argtypes = [vp, fp, C.c_size_t]
+        L.eaadc_precond_get.argtypes = [vp, fp, C.c_size_t]
+        L.eaadc_precond_pairs.argtypes = [vp, C.c_int, C.c_int, vp, vp, dp, vp, vp, vp, vp, vp, vp]
+        L.eaadc_mlp_forward.argtypes = [vp, C.c_longlong, vp, vp, vp]
+        L.eaadc_mlp_loss_grad.argtypes = [vp, C.c_int, ip, vp, vp, vp, vp, dp, fp, vp]
+        L.eaadc_mlp_train_step.argtypes = [vp, C.c_int, ip, vp, vp, vp, vp, C.c_float, dp, vp]
+        L.eaadc_get_trace.argtypes = [vp, C.c_int, ip, ip, dp, dp, dp]
         L.eaadc_num_states.restype = C.c_int
         L.eaadc_get_m11.argtypes = [vp, C.c_int, dp]
         L.eaadc_davidson.argtypes = [vp, C.c_int, C.POINTER(DavidsonOpts), dp, dp, ip]
@@ -178,7 +190,7 @@ def eaadc_eigh_sym(n, a_ptr, w_ptr, v_ptr, device=0, stream=None):
 
 
 def _opts(d):
-    base = dict(tol=1e-8, etol=1e-10, maxit=300, max_sub=40, prec=EAADC_FP64, refine=0)
+    base = dict(tol=1e-8, etol=1e-10, maxit=300, max_sub=40, prec=EAADC_FP64, refine=0, precond=0, trace=0)
     base.update(d)
     return base
 
@@ -201,10 +213,11 @@ def eaadc_num_states(ctx):
     return lib().eaadc_num_states(ctx)
 
 
-def eaadc_davidson(ctx, nroots, tol=1e-6, etol=1e-10, maxit=200, max_sub=40, prec=EAADC_FP64, refine=1):
+def eaadc_davidson(ctx, nroots, tol=1e-6, etol=1e-10, maxit=200, max_sub=40, prec=EAADC_FP64, refine=1,
+                   precond=0, trace=0):
     """Returns (omega[nstates, nroots], resnorm[nstates, nroots], iters[nstates], status)."""
     nstates = eaadc_num_states(ctx)
-    opts = DavidsonOpts(tol, etol, maxit, max_sub, prec, refine)
+    opts = DavidsonOpts(tol, etol, maxit, max_sub, prec, refine, precond, trace)
     om = np.zeros((max(nstates, 1), nroots))
     rn = np.zeros((max(nstates, 1), nroots))
     it = np.zeros(max(nstates, 1), dtype=np.int32)
@@ -213,6 +226,69 @@ def eaadc_davidson(ctx, nroots, tol=1e-6, etol=1e-10, maxit=200, max_sub=40, pre
     if st not in (EAADC_OK, EAADC_ERR_NOCONV):
         _check(ctx, st)
     return om, rn, it, st
+
+
+def _fp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def eaadc_precond_load(ctx, weights):
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _check(ctx, lib().eaadc_precond_load(ctx, _fp(w), w.nbytes))
+
+
+def eaadc_precond_get(ctx):
+    w = np.empty(MLP_PARAMS, dtype=np.float32)
+    _check(ctx, lib().eaadc_precond_get(ctx, _fp(w), w.nbytes))
+    return w
+
+
+def eaadc_precond_pairs(ctx, state, nvec, y_ptr, r_ptr, theta, ystar_ptr, feat_ptr, rr_ptr, base_ptr, target_ptr,
+                        stream=None):
+    """Device pointers (see include/eaadc.h); theta: host sequence of nvec Ritz values."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    vp_ = lambda p: C.c_void_p(p) if p else None  # noqa: E731
+    _check(ctx, lib().eaadc_precond_pairs(ctx, state, nvec, vp_(y_ptr), vp_(r_ptr), _dp(th), vp_(ystar_ptr),
+                                          vp_(feat_ptr), vp_(rr_ptr), vp_(base_ptr), vp_(target_ptr), stream))
+
+
+def eaadc_mlp_forward(ctx, n, feat_ptr, m_ptr, stream=None):
+    _check(ctx, lib().eaadc_mlp_forward(ctx, n, C.c_void_p(feat_ptr), C.c_void_p(m_ptr), stream))
+
+
+def eaadc_mlp_loss_grad(ctx, segs, feat_ptr, rr_ptr, base_ptr, target_ptr, stream=None):
+    sg = np.ascontiguousarray(segs, dtype=np.int32)
+    L = np.zeros(1)
+    g = np.empty(MLP_PARAMS, dtype=np.float32)
+    _check(ctx, lib().eaadc_mlp_loss_grad(ctx, sg.size - 1, _ip(sg), C.c_void_p(feat_ptr), C.c_void_p(rr_ptr),
+                                          C.c_void_p(base_ptr), C.c_void_p(target_ptr), _dp(L), _fp(g), stream))
+    return float(L[0]), g
+
+
+def eaadc_mlp_train_step(ctx, segs, feat_ptr, rr_ptr, base_ptr, target_ptr, lr, stream=None):
+    sg = np.ascontiguousarray(segs, dtype=np.int32)
+    L = np.zeros(1)
+    _check(ctx, lib().eaadc_mlp_train_step(ctx, sg.size - 1, _ip(sg), C.c_void_p(feat_ptr), C.c_void_p(rr_ptr),
+                                           C.c_void_p(base_ptr), C.c_void_p(target_ptr), C.c_float(lr), _dp(L),
+                                           stream))
+    return float(L[0])
+
+
+def eaadc_get_trace(ctx, state=0):
+    """(X [niters, nroots, dim], R [niters, nroots, dim], theta [niters, nroots]) of the last traced Davidson."""
+    ni, nr = C.c_int(), C.c_int()
+    _check(ctx, lib().eaadc_get_trace(ctx, state, C.byref(ni), C.byref(nr), None, None, None))
+    dim = eaadc_state_info(ctx, state)[2]
+    X = np.empty((ni.value, nr.value, dim))
+    R = np.empty_like(X)
+    th = np.empty((ni.value, nr.value))
+    if ni.value * nr.value:
+        _check(ctx, lib().eaadc_get_trace(ctx, state, C.byref(ni), C.byref(nr), _dp(X), _dp(R), _dp(th)))
+    return X, R, th
 
 
 def eaadc_get_eigvecs(ctx, state, nroots):

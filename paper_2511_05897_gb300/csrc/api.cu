@@ -138,6 +138,7 @@ eaadc_davidson_opts inner_opts(const eaadc_davidson_opts* o) {
   }
   eaadc_davidson_opts d;
   d.tol = 1e-8; d.etol = 1e-10; d.maxit = 300; d.max_sub = 40; d.prec = EAADC_FP64; d.refine = 0;
+  d.precond = 0; d.trace = 0;
   return d;
 }
 }  // namespace
@@ -261,6 +262,102 @@ eaadc_status eaadc_get_m11(eaadc_ctx* ctx, int state, double* m11_host) {
   });
 }
 
+eaadc_status eaadc_precond_load(eaadc_ctx* ctx, const float* weights, size_t bytes) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    if (!weights || bytes != sizeof(float) * (size_t)ea::kMlpParams)
+      ea::fail(EAADC_ERR_ARG, "weights must be EAADC_MLP_PARAMS floats");
+    for (long long i = 0; i < ea::kMlpParams; ++i)
+      if (!std::isfinite(weights[i])) ea::fail(EAADC_ERR_NONFINITE, "non-finite weight");
+    set_device(ctx);
+    ea::mlp_load(ctx->stream, ctx->mlp, weights);
+  });
+}
+
+eaadc_status eaadc_precond_get(eaadc_ctx* ctx, float* weights, size_t bytes) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    if (!weights || bytes != sizeof(float) * (size_t)ea::kMlpParams)
+      ea::fail(EAADC_ERR_ARG, "weights must be EAADC_MLP_PARAMS floats");
+    if (!ctx->mlp.ready) ea::fail(EAADC_ERR_STATE, "no weights loaded");
+    set_device(ctx);
+    EA_CK(cudaMemcpyAsync(weights, ctx->mlp.w.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    EA_CK(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+eaadc_status eaadc_precond_pairs(eaadc_ctx* ctx, int state, int nvec, const double* y_dev, const double* r_dev,
+                                 const double* theta_host, const double* ystar_dev, float* feat_dev, float* rr_dev,
+                                 float* base_dev, float* target_dev, void* stream) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    ea::State& st = get_state(ctx, state);
+    if (nvec < 1 || !y_dev || !r_dev || !theta_host || !feat_dev || !rr_dev || !base_dev)
+      ea::fail(EAADC_ERR_ARG, "bad arguments");
+    if ((ystar_dev == nullptr) != (target_dev == nullptr)) ea::fail(EAADC_ERR_ARG, "ystar and target go together");
+    ea::precond_pairs((cudaStream_t)stream, st, nvec, y_dev, r_dev, theta_host, ystar_dev, feat_dev, rr_dev,
+                      base_dev, target_dev);
+  });
+}
+
+eaadc_status eaadc_mlp_forward(eaadc_ctx* ctx, long long n, const float* feat_dev, float* m_dev, void* stream) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    if (n < 1 || !feat_dev || !m_dev) ea::fail(EAADC_ERR_ARG, "bad arguments");
+    set_device(ctx);
+    ea::mlp_forward((cudaStream_t)stream, ctx->mlp, n, feat_dev, m_dev);
+  });
+}
+
+eaadc_status eaadc_mlp_loss_grad(eaadc_ctx* ctx, int nseg, const int* seg_host, const float* feat_dev,
+                                 const float* rr_dev, const float* base_dev, const float* target_dev,
+                                 double* loss_host, float* grad_host, void* stream) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    if (nseg < 1 || !seg_host || !feat_dev || !rr_dev || !base_dev || !target_dev) ea::fail(EAADC_ERR_ARG, "bad arguments");
+    set_device(ctx);
+    cudaStream_t s = (cudaStream_t)stream;
+    const double L = ea::mlp_loss_grad(s, ctx->mlp, nseg, seg_host, feat_dev, rr_dev, base_dev, target_dev, 0.f, false);
+    if (loss_host) *loss_host = L;
+    if (grad_host) {
+      EA_CK(cudaMemcpyAsync(grad_host, ctx->mlp.g.p, sizeof(float) * ea::kMlpParams, cudaMemcpyDeviceToHost, s));
+      EA_CK(cudaStreamSynchronize(s));
+    }
+  });
+}
+
+eaadc_status eaadc_mlp_train_step(eaadc_ctx* ctx, int nseg, const int* seg_host, const float* feat_dev,
+                                  const float* rr_dev, const float* base_dev, const float* target_dev, float lr,
+                                  double* loss_host, void* stream) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    if (nseg < 1 || !seg_host || !feat_dev || !rr_dev || !base_dev || !target_dev || !(lr > 0))
+      ea::fail(EAADC_ERR_ARG, "bad arguments");
+    set_device(ctx);
+    const double L = ea::mlp_loss_grad((cudaStream_t)stream, ctx->mlp, nseg, seg_host, feat_dev, rr_dev, base_dev,
+                                       target_dev, lr, true);
+    if (loss_host) *loss_host = L;
+  });
+}
+
+eaadc_status eaadc_get_trace(eaadc_ctx* ctx, int state, int* niters, int* nroots, double* x_host, double* r_host,
+                             double* theta_host) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    ea::State& st = get_state(ctx, state);
+    if (niters) *niters = st.trN;
+    if (nroots) *nroots = st.trK;
+    const size_t cnt = (size_t)st.trN * st.trK;
+    if (!cnt) return;
+    if (x_host) EA_CK(cudaMemcpyAsync(x_host, st.trX.p, sizeof(double) * cnt * st.dim, cudaMemcpyDeviceToHost, ctx->stream));
+    if (r_host) EA_CK(cudaMemcpyAsync(r_host, st.trR.p, sizeof(double) * cnt * st.dim, cudaMemcpyDeviceToHost, ctx->stream));
+    if (theta_host) std::memcpy(theta_host, st.trTheta.data(), sizeof(double) * cnt);
+    EA_CK(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
 int eaadc_num_states(const eaadc_ctx* ctx) { return ctx ? (int)ctx->states.size() : 0; }
 
 eaadc_status eaadc_davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts* opts, double* omega,
@@ -274,6 +371,8 @@ eaadc_status eaadc_davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opt
     if (!(opts->tol > 0) || opts->maxit < 1) ea::fail(EAADC_ERR_ARG, "bad Davidson options");
     if (opts->prec != EAADC_FP64 && opts->prec != EAADC_MIXED_BF16 && opts->prec != EAADC_MIXED_BF16X3)
       ea::fail(EAADC_ERR_ARG, "unknown precision");
+    if (opts->precond != 0 && opts->precond != 1) ea::fail(EAADC_ERR_ARG, "unknown preconditioner");
+    if (opts->trace < 0 || opts->trace > 10000) ea::fail(EAADC_ERR_ARG, "trace must be in [0, 10000]");
     ea::davidson(ctx, nroots, *opts, omega, resnorm, iters, &conv);
   });
   if (st == EAADC_OK && !conv) {

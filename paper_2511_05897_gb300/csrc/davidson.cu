@@ -217,11 +217,68 @@ static void apply_sigma(cudaStream_t s, State& st, int prec, int nvec, const dou
   else sigma_mixed(s, st, nvec, x, y, prec == EAADC_MIXED_BF16X3);
 }
 
+__global__ void gather_scalars(const double* __restrict__ src, const int* __restrict__ idx, int n,
+                               double* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+
+__global__ void gather_rows(const double* __restrict__ src, const int* __restrict__ idx, int nr, long long n,
+                            double* __restrict__ dst) {
+  const long long total = (long long)nr * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = src[(long long)idx[e / n] * n + e % n];
+}
+
+// Dn[j] = rr (1/(theta - D) + m) for the selected rows j (a non-finite m keeps
+// the diagonal term)
+__global__ void learned_combine(const float* __restrict__ base, const float* __restrict__ rr,
+                                const float* __restrict__ m, const int* __restrict__ jrows, int nl, long long n,
+                                double* __restrict__ Dn) {
+  const long long total = (long long)nl * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e / n);
+    const long long i = e % n;
+    const float mi = m[e];
+    Dn[(long long)jrows[q] * n + i] = (double)base[e] + (isfinite(mi) ? (double)rr[e] * (double)mi : 0.0);
+  }
+}
+
+static void learned_correction(cudaStream_t s, State& st, const Mlp& mlp, const double* R, const double* theta,
+                               const double* rnorm, const std::vector<int>& un, const std::vector<int>& lr, long long n,
+                               double* Dn, DArr<float>& feat, DArr<float>& rr, DArr<float>& base, DArr<float>& m,
+                               DArr<double>& thd, DArr<double>& rnd) {
+  const int nl = (int)lr.size();
+  std::vector<int> roots(nl);
+  for (int q = 0; q < nl; ++q) roots[q] = un[lr[q]];
+  DArr<int> ridx((size_t)nl, s), jidx((size_t)nl, s);
+  EA_CK(cudaMemcpyAsync(ridx.p, roots.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s));
+  EA_CK(cudaMemcpyAsync(jidx.p, lr.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s));
+  const size_t rows = (size_t)nl * n;
+  if (feat.n < rows * kMlpF) {
+    feat.alloc(rows * kMlpF, s);
+    rr.alloc(rows, s);
+    base.alloc(rows, s);
+    m.alloc(rows, s);
+  }
+  DArr<double> Rsel(rows, s);
+  gather_rows<<<gridn((long long)rows), 256, 0, s>>>(R, ridx.p, nl, n, Rsel.p);
+  EA_LAUNCH();
+  gather_scalars<<<1, 128, 0, s>>>(theta, ridx.p, nl, thd.p);
+  EA_LAUNCH();
+  gather_scalars<<<1, 128, 0, s>>>(rnorm, ridx.p, nl, rnd.p);
+  EA_LAUNCH();
+  precond_features(s, st, nl, Rsel.p, thd.p, rnd.p, feat.p, rr.p, base.p);
+  mlp_forward(s, mlp, (long long)rows, feat.p, m.p);
+  learned_combine<<<gridn((long long)rows), 256, 0, s>>>(base.p, rr.p, m.p, jidx.p, nl, n, Dn);
+  EA_LAUNCH();
+}
+
 // One Davidson phase at precision `prec` starting from `k0` orthonormal rows in V.
 // Returns true if converged.
 static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaadc_davidson_opts& opt, DArr<double>& V,
                            DArr<double>& S, int mmax, int k0, std::vector<double>& theta, std::vector<double>& rn,
-                           int& iters, DArr<double>& Xr, bool stop_at_floor) {
+                           int& iters, DArr<double>& Xr, bool stop_at_floor, const Mlp* mlp) {
   const long long n = st.dim;
   int m = k0;
   apply_sigma(s, st, prec, m, V.p, S.p);
@@ -234,6 +291,12 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
   DArr<double> part((size_t)k * nb, s);
   std::vector<double> th_old(k, INFINITY);
   std::vector<double> hist;  // largest residual norm per iteration
+  // learned correction: per root, whether its last step used it and whether it fell back
+  const bool learned = opt.precond == 1 && mlp && mlp->ready;
+  std::vector<char> used(k, 0), fell(k, 0);
+  std::vector<double> rn_prev(k, INFINITY);
+  DArr<float> feat, lrr, lbase, lm;
+  DArr<double> thd((size_t)k, s), rnd2((size_t)k, s);
   theta.assign(k, 0.0);
   rn.assign(k, 0.0);
   bool conv = false;
@@ -270,6 +333,21 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
       if (rn[r] > opt.tol) un.push_back(r);
     }
     th_old = theta;
+    if (opt.trace > 0 && st.trN < opt.trace) {
+      if (st.trN == 0 || st.trK != k) {
+        st.trK = k;
+        st.trN = 0;
+        st.trX.alloc((size_t)opt.trace * k * n, s);
+        st.trR.alloc((size_t)opt.trace * k * n, s);
+        st.trTheta.clear();
+      }
+      EA_CK(cudaMemcpyAsync(st.trX.p + (long long)st.trN * k * n, Xr.p, sizeof(double) * k * n,
+                            cudaMemcpyDeviceToDevice, s));
+      EA_CK(cudaMemcpyAsync(st.trR.p + (long long)st.trN * k * n, R.p, sizeof(double) * k * n,
+                            cudaMemcpyDeviceToDevice, s));
+      st.trTheta.insert(st.trTheta.end(), theta.begin(), theta.end());
+      ++st.trN;
+    }
     if (all) { conv = true; break; }
     // reduced precision: stop at the noise floor of the mixed sigma (the
     // largest residual shrank by less than 2x over the last 8 iterations)
@@ -282,6 +360,18 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
     EA_CK(cudaMemcpyAsync(rows.p, un.data(), sizeof(int) * nn, cudaMemcpyHostToDevice, s));
     precond_kernel<<<dim3(nb, nn), 256, 0, s>>>(R.p, w.p, st.diag.p, rows.p, nn, n, Dn.p);
     EA_LAUNCH();
+    if (learned) {
+      // a root whose residual grew after a learned step falls back to the diagonal correction
+      std::vector<int> lr;
+      for (int j = 0; j < nn; ++j) {
+        const int r = un[j];
+        if (used[r] && rn[r] >= rn_prev[r]) fell[r] = 1;
+        used[r] = !fell[r];
+        if (used[r]) lr.push_back(j);
+      }
+      for (int r = 0; r < k; ++r) rn_prev[r] = rn[r];
+      if (!lr.empty()) learned_correction(s, st, *mlp, R.p, w.p, rnd.p, un, lr, n, Dn.p, feat, lrr, lbase, lm, thd, rnd2);
+    }
     row_norms(s, Dn.p, nn, n, nrm.p);
     scale_rows<<<dim3(nb, nn), 256, 0, s>>>(Dn.p, n, nrm.p);
     EA_LAUNCH();
@@ -320,7 +410,10 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
 }
 
 bool davidson_state(cudaStream_t s, State& st, int nroots, const eaadc_davidson_opts& opt, double* omega,
-                    double* resnorm, int* iters) {
+                    double* resnorm, int* iters, const Mlp* mlp) {
+  if (opt.precond == 1 && !(mlp && mlp->ready))
+    fail(EAADC_ERR_STATE, "learned correction requested but no weights loaded (eaadc_precond_load)");
+  st.trN = 0;
   const long long n = st.dim;
   int k = (int)std::min<long long>(nroots, n);
   int mmax = (int)std::min<long long>(std::min(opt.max_sub, 96), n);
@@ -345,11 +438,11 @@ bool davidson_state(cudaStream_t s, State& st, int nroots, const eaadc_davidson_
   std::vector<double> theta, rn;
   int it = 0;
   const bool refine = opt.prec != EAADC_FP64 && opt.refine;
-  bool conv = davidson_phase(s, st, k, opt.prec, opt, V, S, mmax, k, theta, rn, it, st.evecs, refine);
+  bool conv = davidson_phase(s, st, k, opt.prec, opt, V, S, mmax, k, theta, rn, it, st.evecs, refine, mlp);
   if (refine) {
     // FP64 refinement from the mixed-precision Ritz vectors
     EA_CK(cudaMemcpyAsync(V.p, st.evecs.p, sizeof(double) * k * n, cudaMemcpyDeviceToDevice, s));
-    conv = davidson_phase(s, st, k, EAADC_FP64, opt, V, S, mmax, k, theta, rn, it, st.evecs, false);
+    conv = davidson_phase(s, st, k, EAADC_FP64, opt, V, S, mmax, k, theta, rn, it, st.evecs, false, mlp);
   }
   for (int r = 0; r < k; ++r) {
     omega[r] = theta[r];
@@ -370,7 +463,7 @@ void davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opts& opt, double
   for (size_t si = 0; si < ctx->states.size(); ++si) {
     State& st = *ctx->states[si];
     const bool conv = davidson_state(ctx->stream, st, nroots, opt, omega + si * nroots,
-                                     resnorm ? resnorm + si * nroots : nullptr, iters ? iters + si : nullptr);
+                                     resnorm ? resnorm + si * nroots : nullptr, iters ? iters + si : nullptr, &ctx->mlp);
     if (st.ref1p.p) pick_target(ctx->stream, st);
     *converged &= conv;
   }

@@ -159,6 +159,10 @@ struct State {
   int vfull = 0, nauxfull = 0;                 // untruncated sizes
   std::vector<double> omega;                   // roots of the last Davidson
   int target = -1;                             // index of the target root
+  // Davidson trace (opts.trace > 0): Ritz vectors, residuals and values per iteration
+  DArr<double> trX, trR;
+  std::vector<double> trTheta;
+  int trN = 0, trK = 0;
   long long bvv_pitch = 0, bb_pitch = 0;      // row pitches (elements) of Bvv_bf and Bb_bf
   DArr<int> err;                              // device error word of bounded waits
   bool mixed_ready = false;
@@ -166,6 +170,28 @@ struct State {
   DArr<double> evecs;             // [nroots][dim]
   int nvecs = 0;
 };
+
+// Learned Davidson correction: per-element MLP (16 features -> 3 x 256 tanh
+// -> 1), FP32 master weights with Adam moments, flat layout
+// W1[256][16] b1 W2[256][256] b2 W3[256][256] b3 w4[256] b4.
+constexpr int kMlpF = 16, kMlpW = 256;
+constexpr long long kMlpParams = 136193;
+struct Mlp {
+  DArr<float> w, g, mom, vel;
+  int step = 0;
+  bool ready = false;
+};
+// m[i] = MLP(feat[i]) for n rows (activations allocated on s).
+void mlp_forward(cudaStream_t s, const Mlp& net, long long n, const float* feat, float* m);
+// Features, normalised residual rr and diagonal term base = rr / (theta - D)
+// of nvec residual vectors R (rows of length st.dim) with Ritz values theta.
+void precond_features(cudaStream_t s, const State& st, int nvec, const double* R, const double* theta_dev,
+                      const double* rnorm_dev, float* feat, float* rr, float* base);
+void precond_pairs(cudaStream_t s, const State& st, int nvec, const double* Y, const double* R,
+                   const double* theta_host, const double* Ys, float* feat, float* rr, float* base, float* T);
+double mlp_loss_grad(cudaStream_t s, Mlp& net, int nseg, const int* segs_host, const float* feat, const float* rr,
+                     const float* base, const float* T, float lr, bool update);
+void mlp_load(cudaStream_t s, Mlp& net, const float* host);
 
 }  // namespace ea
 
@@ -175,6 +201,7 @@ struct eaadc_ctx {
   int o = 0, v = 0, naux = 0;
   ea::DArr<double> eo, ev, Boo, Bov, Bvv;
   std::vector<ea::State*> states;
+  ea::Mlp mlp;
   std::string err;
   ~eaadc_ctx();
 };
@@ -205,7 +232,7 @@ void make_diagonal(cudaStream_t s, State& st);
 // Lowest nroots roots of one state (Ritz vectors into st.evecs, values into
 // st.omega); returns true if converged.
 bool davidson_state(cudaStream_t s, State& st, int nroots, const eaadc_davidson_opts& opt, double* omega,
-                    double* resnorm, int* iters);
+                    double* resnorm, int* iters, const Mlp* mlp = nullptr);
 // Target root of an FNO state: largest |overlap| of the 1p part with ref1p.
 void pick_target(cudaStream_t s, State& st);
 // Per-state FNO/NAF truncated states replacing ctx->states (Sec. III) and
