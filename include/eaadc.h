@@ -68,9 +68,14 @@ typedef struct {
   int prec;       /* eaadc_prec used for the sigma vectors inside the loop; a
                      reduced-precision phase stops at its noise floor (largest
                      residual shrinking by less than 2x in 8 iterations) */
-  int refine;     /* 1: after a mixed-precision solve, FP64 sigma of the Ritz
-                     vectors and FP64 Rayleigh-Ritz, then FP64 Davidson
-                     iterations until tol is met in FP64 */
+  int refine;     /* after a reduced-precision phase (which stops at tol or at
+                     its noise floor): 1 = FP64 Davidson iterations from its
+                     Ritz vectors until tol is met in FP64; 2 = one FP64 sigma
+                     of the Ritz vectors and a Rayleigh-Ritz step in their
+                     span (Ritz values exact to second order in the error of
+                     the vectors; resnorm reports the FP64 residuals); 3 = as
+                     2 with the split-BF16 sigma (EAADC_MIXED_BF16X3, about
+                     1e-5 relative) instead of FP64 */
   int precond;    /* 0: diagonal correction r/(theta - D); 1: learned
                      correction (weights from eaadc_precond_load), falling
                      back to the diagonal one, for the rest of the solve, for

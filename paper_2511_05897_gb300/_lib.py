@@ -145,10 +145,13 @@ def eaadc_sigma(ctx, state, nvec, x_ptr, sigma_ptr, prec=EAADC_FP64, stream=None
     _check(ctx, lib().eaadc_sigma(ctx, state, nvec, C.c_void_p(x_ptr), C.c_void_p(sigma_ptr), prec, stream))
 
 
-def eaadc_sigma_host(ctx, state, x, prec=EAADC_FP64):
+def eaadc_sigma_host(ctx, state, x, prec=EAADC_FP64, out=None):
+    """Host arrays; out (optional, e.g. pinned memory) receives sigma."""
     x = _f64(x)
     nvec = 1 if x.ndim == 1 else x.shape[0]
-    y = np.empty_like(x)
+    y = np.empty_like(x) if out is None else out
+    if y.shape != x.shape or y.dtype != np.float64 or not y.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 array shaped like x")
     _check(ctx, lib().eaadc_sigma_host(ctx, state, nvec, _dp(x), _dp(y), prec))
     return y
 

@@ -372,6 +372,7 @@ eaadc_status eaadc_davidson(eaadc_ctx* ctx, int nroots, const eaadc_davidson_opt
     if (opts->prec != EAADC_FP64 && opts->prec != EAADC_MIXED_BF16 && opts->prec != EAADC_MIXED_BF16X3)
       ea::fail(EAADC_ERR_ARG, "unknown precision");
     if (opts->precond != 0 && opts->precond != 1) ea::fail(EAADC_ERR_ARG, "unknown preconditioner");
+    if (opts->refine < 0 || opts->refine > 3) ea::fail(EAADC_ERR_ARG, "refine must be 0..3");
     if (opts->trace < 0 || opts->trace > 10000) ea::fail(EAADC_ERR_ARG, "trace must be in [0, 10000]");
     ea::davidson(ctx, nroots, *opts, omega, resnorm, iters, &conv);
   });

@@ -409,6 +409,35 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
   return conv;
 }
 
+// Final sigma-and-Ritz step on the k Ritz vectors in st.evecs: sigma at
+// precision prec (FP64, or the split-BF16 one), Rayleigh-Ritz in their span,
+// residual norms of that sigma.  The Ritz values are then exact to second
+// order in the error of the vectors, up to the error of that sigma.
+static void final_ritz(cudaStream_t s, State& st, int k, int prec, std::vector<double>& theta, std::vector<double>& rn) {
+  const long long n = st.dim;
+  DArr<double> SX((size_t)k * n, s), G((size_t)k * k, s), Gs((size_t)k * k, s), w((size_t)k, s), U((size_t)k * k, s),
+      X2((size_t)k * n, s), S2((size_t)k * n, s), R((size_t)k * n, s), rnd((size_t)k, s);
+  apply_sigma(s, st, prec, k, st.evecs.p, SX.p);
+  gram(s, st.evecs.p, k, SX.p, k, n, G.p, k);
+  symmetrize<<<1, 256, 0, s>>>(G.p, k, k, Gs.p);
+  EA_LAUNCH();
+  jacobi_eigh(s, k, Gs.p, w.p, U.p);
+  dgemm(s, true, false, k, (int)n, k, 1.0, U.p, k, st.evecs.p, n, 0.0, X2.p, n);
+  dgemm(s, true, false, k, (int)n, k, 1.0, U.p, k, SX.p, n, 0.0, S2.p, n);
+  const int nb = std::min(256, (int)std::max<long long>(1, (n + 255) / 256));
+  DArr<double> part((size_t)k * nb, s);
+  residual_kernel<<<dim3(nb, k), 256, 0, s>>>(S2.p, X2.p, w.p, R.p, n, k, part.p);
+  EA_LAUNCH();
+  finish_norms<<<1, 64, 0, s>>>(part.p, nb, k, rnd.p);
+  EA_LAUNCH();
+  EA_CK(cudaMemcpyAsync(st.evecs.p, X2.p, sizeof(double) * k * n, cudaMemcpyDeviceToDevice, s));
+  theta.assign(k, 0.0);
+  rn.assign(k, 0.0);
+  EA_CK(cudaMemcpyAsync(theta.data(), w.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  EA_CK(cudaMemcpyAsync(rn.data(), rnd.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  EA_CK(cudaStreamSynchronize(s));
+}
+
 bool davidson_state(cudaStream_t s, State& st, int nroots, const eaadc_davidson_opts& opt, double* omega,
                     double* resnorm, int* iters, const Mlp* mlp) {
   if (opt.precond == 1 && !(mlp && mlp->ready))
@@ -439,7 +468,10 @@ bool davidson_state(cudaStream_t s, State& st, int nroots, const eaadc_davidson_
   int it = 0;
   const bool refine = opt.prec != EAADC_FP64 && opt.refine;
   bool conv = davidson_phase(s, st, k, opt.prec, opt, V, S, mmax, k, theta, rn, it, st.evecs, refine, mlp);
-  if (refine) {
+  if (refine && (opt.refine == 2 || opt.refine == 3)) {
+    final_ritz(s, st, k, opt.refine == 2 ? EAADC_FP64 : EAADC_MIXED_BF16X3, theta, rn);
+    conv = true;
+  } else if (refine) {
     // FP64 refinement from the mixed-precision Ritz vectors
     EA_CK(cudaMemcpyAsync(V.p, st.evecs.p, sizeof(double) * k * n, cudaMemcpyDeviceToDevice, s));
     conv = davidson_phase(s, st, k, EAADC_FP64, opt, V, S, mmax, k, theta, rn, it, st.evecs, false, mlp);

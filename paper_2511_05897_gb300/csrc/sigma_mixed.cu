@@ -121,15 +121,16 @@ __global__ void fg_operands(const float* __restrict__ F, const float* __restrict
   const long long total = (long long)nvec * n2;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long n = i / n2, r = i % n2;
-    {  // F_n[l][c][d]
+    {  // F_n[l][c][d], stored F[l][n][c][d]
       const int d = r % v, c = (r / v) % v, l = (int)(r / ((long long)v * v));
       const long long row = n * v + c, col = (long long)l * v + d;
-      put(F1a, row, col, (double)F[i]);
-      put(F1b, row, col, (double)F[i]);
+      const float f = F[(((long long)l * nvec + n) * v + c) * v + d];
+      put(F1a, row, col, (double)f);
+      put(F1b, row, col, (double)f);
     }
-    {  // G_n[b][l][d]
+    {  // G_n[b][l][d], stored G[b][n][l][d]
       const int d = r % v, l = (r / v) % o, b = (int)(r / ov);
-      put(G1, n * v + b, (long long)l * v + d, (double)G[i]);
+      put(G1, n * v + b, (long long)l * v + d, (double)G[(((long long)b * nvec + n) * o + l) * v + d]);
     }
   }
 }
@@ -144,8 +145,8 @@ __global__ void h_from_tc(const float* __restrict__ H1, const float* __restrict_
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
     const long long n = i / n2, r = i % n2;
     const int t = r % v, q = (r / v) % v, p = (int)(r / ((long long)v * v));
-    h1[i] = H1[((long long)p * v + q) * nv + n * v + t];         // l=p, d=q, c=t
-    h3[i] = H23[(ov + (long long)p * v + t) * nv + n * v + q];  // l=p, b=q, d=t
+    h1[i] = H1[((long long)p * v + t) * nv + n * v + q];         // h1[n][l][c][d]: l=p, c=q, d=t
+    h3[i] = H23[(ov + (long long)p * v + t) * nv + n * v + q];  // h3[n][l][b][d]: l=p, b=q, d=t
     const long long b = r / ov, l = (r / v) % o, d = r % v;
     h2[i] = H23[(l * v + d) * nv + n * v + b];
   }
@@ -226,9 +227,18 @@ __global__ void split_f32(const float* __restrict__ in, bf16* __restrict__ hi, b
   }
 }
 
-__global__ void add_f32(const float* __restrict__ a, double* __restrict__ y, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] += (double)a[i];
+// Yt[a][n] = x[n][a] for the 1p parts (a < v)
+__global__ void gather_1p(const float* __restrict__ x, long long dim, int v, int nvec, float* __restrict__ Yt) {
+  const int total = v * nvec;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+    Yt[i] = x[(long long)(i % nvec) * dim + i / nvec];
+}
+
+// y[n][a] += sy[a][n]
+__global__ void add_1p_T(const float* __restrict__ sy, double* __restrict__ y, long long dim, int v, int nvec) {
+  const int total = v * nvec;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+    y[(long long)(i % nvec) * dim + i / nvec] += (double)sy[i];
 }
 
 // BF16 operands of a state (and their low parts when x3): B^Q in [Q][c][e] and
@@ -334,6 +344,54 @@ tc2::Args gargs(int M, int N, int K, int* err) {
   return g;
 }
 
+// DF coupling pieces of all nvec vectors at once (FP32, the vector index n a
+// free index of one operand, so every pass over B^Q serves all vectors):
+// 1p -> 2p1h: CA[n][k][b][c] = sum_Q (sum_a B^Q_ba y_a) B^Q_kc + the o^3 v^2
+// term, and the inputs of the tensor-core o^2 v^3 terms F[l][n][c][d] =
+// sum_Q (sum_a B^Q_la y_a) B^Q_cd, G[b][n][l][d] = sum_Q (sum_a B^Q_ba y_a) B^Q_ld.
+void couple12_nv(cudaStream_t s, const CoupOps<float>& c, const float* x32, long long dim, int nvec, float* CA,
+                 float* F, float* G) {
+  const int o = c.o, v = c.v, naux = c.naux;
+  using TT = TensT<float>;
+  TT Bov{(float*)c.Bov, {naux, o, v}}, Bvv{(float*)c.Bvv, {naux, v, v}}, Boo{(float*)c.Boo, {naux, o, o}};
+  DArr<float> Yt((size_t)v * nvec, s), Qy((size_t)naux * v * nvec, s), Qo((size_t)naux * o * nvec, s),
+      H((size_t)o * o * o * nvec, s);
+  gather_1p<<<gridn((long long)v * nvec), 256, 0, s>>>(x32, dim, v, nvec, Yt.p);
+  EA_LAUNCH();
+  TT Ytt{Yt.p, {v, nvec}}, Qyt{Qy.p, {naux, v, nvec}}, Qot{Qo.p, {naux, o, nvec}};
+  einsumT<float>(s, "Qba,an->Qbn", 1.f, Bvv, Ytt, 0.f, Qyt);  // B^Q symmetric
+  einsumT<float>(s, "Qbn,Qkc->nkbc", 1.f, Qyt, Bov, 0.f, TT{CA, {nvec, o, v, v}});
+  einsumT<float>(s, "Qla,an->Qln", 1.f, Bov, Ytt, 0.f, Qot);
+  einsumT<float>(s, "Qln,Qcd->lncd", 1.f, Qot, Bvv, 0.f, TT{F, {o, nvec, v, v}});
+  einsumT<float>(s, "Qbn,Qld->bnld", 1.f, Qyt, Bov, 0.f, TT{G, {v, nvec, o, v}});
+  einsumT<float>(s, "Qln,Qkm->lnkm", 1.f, Qot, Boo, 0.f, TT{H.p, {o, nvec, o, o}});
+  einsumT<float>(s, "lnkm,lmbc->nkbc", 1.f, TT{H.p, {o, nvec, o, o}}, TT{(float*)c.tau, {o, o, v, v}}, 1.f,
+                 TT{CA, {nvec, o, v, v}});
+}
+
+// 2p1h -> 1p for all vectors: sy[a][n] from V[n][k][b][c] (the S-transformed
+// 2p1h parts) and the tensor-core intermediates h1[n][l][c][d], h2[n][b][l][d],
+// h3[n][l][b][d].
+void couple21_nv(cudaStream_t s, const CoupOps<float>& c, const float* V, int nvec, const float* h1, const float* h2,
+                 const float* h3, float* sy) {
+  const int o = c.o, v = c.v, naux = c.naux;
+  using TT = TensT<float>;
+  TT Bov{(float*)c.Bov, {naux, o, v}}, Bvv{(float*)c.Bvv, {naux, v, v}}, Boo{(float*)c.Boo, {naux, o, o}};
+  TT Vt{(float*)V, {nvec, o, v, v}}, syt{sy, {v, nvec}};
+  DArr<float> g((size_t)naux * v * nvec, s), tt((size_t)naux * nvec * o, s), t2q((size_t)naux * nvec * v, s),
+      H4((size_t)o * o * nvec * o, s);
+  TT gt{g.p, {naux, v, nvec}}, ttt{tt.p, {naux, nvec, o}}, t2qt{t2q.p, {naux, nvec, v}};
+  einsumT<float>(s, "Qkc,nkbc->Qbn", 1.f, Bov, Vt, 0.f, gt);
+  einsumT<float>(s, "Qba,Qbn->an", 1.f, Bvv, gt, 0.f, syt);  // B^Q symmetric
+  einsumT<float>(s, "Qcd,nlcd->Qnl", -1.f, Bvv, TT{(float*)h1, {nvec, o, v, v}}, 0.f, ttt);
+  einsumT<float>(s, "Qld,nbld->Qnb", 1.f, Bov, TT{(float*)h2, {nvec, v, o, v}}, 0.f, t2qt);
+  einsumT<float>(s, "Qba,Qnb->an", -1.f, Bvv, t2qt, 1.f, syt);
+  einsumT<float>(s, "Qbd,nlbd->Qnl", -1.f, Bvv, TT{(float*)h3, {nvec, o, v, v}}, 1.f, ttt);
+  einsumT<float>(s, "lmbc,nkbc->lmnk", 1.f, TT{(float*)c.tau, {o, o, v, v}}, Vt, 0.f, TT{H4.p, {o, o, nvec, o}});
+  einsumT<float>(s, "Qkm,lmnk->Qnl", 1.f, Boo, TT{H4.p, {o, o, nvec, o}}, 1.f, ttt);
+  einsumT<float>(s, "Qla,Qnl->an", 1.f, Bov, ttt, 1.f, syt);
+}
+
 // compact out[r][c] (pitch v) = in[r][c] (pitch ip)
 __global__ void compact_f32(const float* __restrict__ in, long long ip, float* __restrict__ out, long long rows, int v) {
   long long n = rows * v;
@@ -428,10 +486,10 @@ void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y
   DArr<float> x32((size_t)(nvec * dim), s);
   f64_to_f32<<<gridn(nvec * dim), 256, 0, s>>>(x, x32.p, nvec * dim);
   EA_LAUNCH();
-  DArr<float> F((size_t)(nvec * n2), s), G((size_t)(nvec * n2), s), CA((size_t)n2, s);
+  DArr<float> F((size_t)(nvec * n2), s), G((size_t)(nvec * n2), s), CA((size_t)(nvec * n2), s);
+  couple12_nv(s, ops, x32.p, dim, nvec, CA.p, F.p, G.p);
   for (int n = 0; n < nvec; ++n) {
-    couple12<float>(s, ops, x32.p + n * dim, CA.p, nullptr, false, F.p + n * n2, G.p + n * n2);
-    add_S_f32<<<gridn(n2), 256, 0, s>>>(CA.p, y + n * dim, o, v);
+    add_S_f32<<<gridn(n2), 256, 0, s>>>(CA.p + n * n2, y + n * dim, o, v);
     EA_LAUNCH();
   }
   // BF16 operands (and low parts in split mode)
@@ -495,17 +553,15 @@ void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y
   combine_ring_ladder<<<gridn(n2 * nvec), 256, 0, s>>>(y, T1.p, T2.p, L.p, nvec, dim, o, v, nvp, lp);
   EA_LAUNCH();
   // 2p1h -> 1p finishing (FP32, CUDA cores) from the tensor-core H tensors
-  DArr<float> h1((size_t)(nvec * n2), s), h2((size_t)(nvec * n2), s), h3((size_t)(nvec * n2), s), V((size_t)n2, s),
-      sy((size_t)v, s);
+  DArr<float> h1((size_t)(nvec * n2), s), h2((size_t)(nvec * n2), s), h3((size_t)(nvec * n2), s),
+      V((size_t)(nvec * n2), s), sy((size_t)v * nvec, s);
   h_from_tc<<<gridn(nvec * n2), 256, 0, s>>>(H1.p, H23.p, h1.p, h2.p, h3.p, nvec, o, v, nvp);
   EA_LAUNCH();
-  for (int n = 0; n < nvec; ++n) {
-    pair_combineT<float>(s, x32.p + n * dim + v, vv, V.p, vv, o, v, (float)kS1, (float)kS2, 1.f, 0.f);
-    fillT<float>(s, sy.p, (size_t)v, 0.f);
-    couple21<float>(s, ops, V.p, sy.p, nullptr, h1.p + n * n2, h2.p + n * n2, h3.p + n * n2);
-    add_f32<<<gridn(v), 256, 0, s>>>(sy.p, y + n * dim, v);
-    EA_LAUNCH();
-  }
+  for (int n = 0; n < nvec; ++n)
+    pair_combineT<float>(s, x32.p + n * dim + v, vv, V.p + n * n2, vv, o, v, (float)kS1, (float)kS2, 1.f, 0.f);
+  couple21_nv(s, ops, V.p, nvec, h1.p, h2.p, h3.p, sy.p);
+  add_1p_T<<<gridn((long long)v * nvec), 256, 0, s>>>(sy.p, y, dim, v, nvec);
+  EA_LAUNCH();
 }
 
 // Ladder alone, transposed FP32 output [nvec][o][c][b] (= ladder[b][c]), for timing the dominant kernel.
