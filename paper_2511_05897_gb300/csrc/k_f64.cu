@@ -1,4 +1,4 @@
-// FP64 building blocks: batched DGEMM, tensor permutation, pair combinations,
+// FP64 building blocks (and their FP32 forms): batched GEMM, tensor permutation, pair combinations,
 // a two-operand contraction engine and a one-CTA Jacobi eigensolver.
 #include "internal.cuh"
 
@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 
 namespace ea {
 
@@ -91,6 +92,111 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, T alpha
   }
 }
 
+// FP32 GEMM on CUDA cores: 128 x 128 output tile per CTA, K in steps of 8,
+// 256 threads each holding an 8 x 8 block of C (rows ty*4+{0..3} and
+// 64+ty*4+{0..3}, columns likewise from tx), the next K step fetched into
+// registers while the current one is consumed from shared memory (two
+// buffers, one barrier per step).  Same batching and K-split contract as
+// dgemm_kernel.
+constexpr int SBM = 128, SBN = 128, SBK = 8, SLD = SBM + 4;
+
+template <bool TA, bool TB, bool BETA0>
+__global__ void __launch_bounds__(256, 2) sgemm_kernel(int M, int N, int K, float alpha, const float* __restrict__ A,
+                                                       long long lda, const float* __restrict__ B, long long ldb,
+                                                       float beta, float* __restrict__ C, long long ldc, GemmBatch bt,
+                                                       int ksplit, int kchunk, long long spanel) {
+  const int zs = blockIdx.z % ksplit;
+  const int z = blockIdx.z / ksplit;
+  const int z1 = z / bt.nb2, z2 = z % bt.nb2;
+  A += z1 * bt.sA1 + z2 * bt.sA2;
+  B += z1 * bt.sB1 + z2 * bt.sB2;
+  C += z1 * bt.sC1 + z2 * bt.sC2 + (long long)zs * spanel;
+  const int kbeg = zs * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  __shared__ __align__(16) float As[2][SBK][SLD];
+  __shared__ __align__(16) float Bs[2][SBK][SLD];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * SBM, n0 = blockIdx.x * SBN;
+  float ra[4], rb[4];
+  // element r of this thread's share of a 128 x 8 tile: (row, k) coordinates
+  auto a_rc = [&](int r, int& mm, int& kk) {
+    const int e = tid + 256 * r;
+    if (TA) { mm = e % SBM; kk = e / SBM; } else { kk = e % SBK; mm = e / SBK; }
+  };
+  auto b_rc = [&](int r, int& nn, int& kk) {
+    const int e = tid + 256 * r;
+    if (TB) { kk = e % SBK; nn = e / SBK; } else { nn = e % SBN; kk = e / SBN; }
+  };
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int mm, kk;
+      a_rc(r, mm, kk);
+      const int gm = m0 + mm, gk = k0 + kk;
+      ra[r] = (gm < M && gk < kend) ? (TA ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk]) : 0.f;
+      int nn;
+      b_rc(r, nn, kk);
+      const int gn = n0 + nn, gk2 = k0 + kk;
+      rb[r] = (gn < N && gk2 < kend) ? (TB ? B[(long long)gn * ldb + gk2] : B[(long long)gk2 * ldb + gn]) : 0.f;
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int mm, kk;
+      a_rc(r, mm, kk);
+      As[buf][kk][mm] = ra[r];
+      int nn;
+      b_rc(r, nn, kk);
+      Bs[buf][kk][nn] = rb[r];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  int buf = 0;
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stash(0);
+  }
+  __syncthreads();
+  for (int k0 = kbeg; k0 < kend; k0 += SBK) {
+    const bool more = k0 + SBK < kend;
+    if (more) fetch(k0 + SBK);
+#pragma unroll
+    for (int kk = 0; kk < SBK; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + tx * 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int gm = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int gn = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+      if (gn >= N) continue;
+      float* c = C + (long long)gm * ldc + gn;
+      *c = BETA0 ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
+    }
+  }
+}
+
 template <class T>
 __global__ void splitk_reduce(const T* __restrict__ P, int ksplit, long long panel, int M, int N,
                               T beta, T* __restrict__ C, long long ldc) {
@@ -103,9 +209,46 @@ __global__ void splitk_reduce(const T* __restrict__ P, int ksplit, long long pan
   }
 }
 
+template <bool TA, bool TB>
+void sgemm_t(cudaStream_t s, int M, int N, int K, float alpha, const float* A, long long lda, const float* B,
+             long long ldb, float beta, float* C, long long ldc, const GemmBatch& bt) {
+  const int nbatch = bt.nb1 * bt.nb2;
+  const long long tiles = (long long)((N + SBN - 1) / SBN) * ((M + SBM - 1) / SBM) * nbatch;
+  // split K when the output grid cannot fill the GPU twice and K is long
+  int ksplit = 1;
+  if (nbatch == 1 && tiles < 304 && K >= 512) {
+    ksplit = (int)std::min<long long>(std::min<long long>((608 + tiles - 1) / tiles, K / 128), 64);
+    if (ksplit < 2) ksplit = 1;
+  }
+  if (ksplit == 1) {
+    dim3 grid((N + SBN - 1) / SBN, (M + SBM - 1) / SBM, nbatch);
+    if (beta == 0.f)
+      sgemm_kernel<TA, TB, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, 1, K, 0);
+    else
+      sgemm_kernel<TA, TB, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt, 1, K, 0);
+    EA_LAUNCH();
+    return;
+  }
+  const int kchunk = ((K + ksplit - 1) / ksplit + SBK - 1) / SBK * SBK;
+  ksplit = (K + kchunk - 1) / kchunk;
+  const long long panel = (long long)M * N;
+  DArr<float> P((size_t)(panel * ksplit), s);
+  dim3 grid((N + SBN - 1) / SBN, (M + SBM - 1) / SBM, ksplit);
+  sgemm_kernel<TA, TB, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, 0.f, P.p, N, bt, ksplit, kchunk,
+                                                  panel);
+  EA_LAUNCH();
+  splitk_reduce<<<(int)std::min<long long>((panel + 255) / 256, 4096), 256, 0, s>>>(P.p, ksplit, panel, M, N, beta,
+                                                                                   C, ldc);
+  EA_LAUNCH();
+}
+
 template <class T, bool TA, bool TB>
 void dgemm_t(cudaStream_t s, int M, int N, int K, T alpha, const T* A, long long lda,
              const T* B, long long ldb, T beta, T* C, long long ldc, const GemmBatch& bt) {
+  if constexpr (std::is_same<T, float>::value) {
+    sgemm_t<TA, TB>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
+    return;
+  }
   const int nbatch = bt.nb1 * bt.nb2;
   const long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * nbatch;
   // split K when the output grid cannot fill the GPU and K is long
