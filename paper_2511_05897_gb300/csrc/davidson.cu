@@ -173,32 +173,104 @@ __global__ void canon_coef(const double* __restrict__ Z, const double* __restric
   *cnt = c;
 }
 
+// Out[r][i] = alpha sum_j coef[j][r] In[j][i] + beta Out[r][i] for r in a block
+// of 16 rows (blockIdx.y), j < m, grid-stride over i: one pass over In per
+// block of 16 output rows.
+__global__ void rowcomb_kernel(int k, long long n, int m, double alpha, const double* __restrict__ coef, int ldc,
+                               const double* __restrict__ In, double beta, double* __restrict__ Out) {
+  __shared__ double cs[96][16];
+  const int r0 = blockIdx.y * 16;
+  const int kr = min(16, k - r0);
+  for (int e = threadIdx.x; e < m * 16; e += blockDim.x) {
+    const int j = e / 16, r = e % 16;
+    cs[j][r] = r < kr ? coef[(long long)j * ldc + r0 + r] : 0.0;
+  }
+  __syncthreads();
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double acc[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc[r] = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double x = In[(long long)j * n + i];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) acc[r] = fma(cs[j][r], x, acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      if (r < kr) {
+        double* o = Out + (long long)(r0 + r) * n + i;
+        *o = beta == 0.0 ? alpha * acc[r] : alpha * acc[r] + beta * *o;
+      }
+    }
+  }
+}
+
+// Partial inner products P[z][a][b] = sum_{t in chunk z} A[a][t] B[b][t] for a
+// block of 8 rows of A (blockIdx.y) and 4 rows of B (blockIdx.z).
+__global__ void gram_partial(const double* __restrict__ A, int ma, const double* __restrict__ B, int mb, long long n,
+                             long long chunk, double* __restrict__ P) {
+  const int a0 = blockIdx.y * 8, b0 = blockIdx.z * 4;
+  const int na = min(8, ma - a0), nb = min(4, mb - b0);
+  const long long t0 = (long long)blockIdx.x * chunk, t1 = min(n, t0 + chunk);
+  double acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    double bv[4], av[8];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bv[b] = b < nb ? B[(long long)(b0 + b) * n + t] : 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) av[a] = a < na ? A[(long long)(a0 + a) * n + t] : 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+  }
+  __shared__ double red[8][32];  // [warp][a*4+b]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      double v = acc[a][b];
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][a * 4 + b] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int a = threadIdx.x / 4, b = threadIdx.x % 4;
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+    if (a < na && b < nb) P[((long long)blockIdx.x * ma + a0 + a) * mb + b0 + b] = v;
+  }
+}
+
 }  // namespace
+
+// Out[r][i] = alpha sum_j coef[j*ldc + r] In[j][i] + beta Out[r][i], r < k,
+// j < m (m <= 96), rows of length n: the subspace updates of the solver.
+static void rowcomb(cudaStream_t s, int k, long long n, int m, double alpha, const double* coef, int ldc,
+                    const double* In, double beta, double* Out) {
+  if (k <= 0 || n <= 0) return;
+  if (m > 96) fail(EAADC_ERR_ARG, "rowcomb: more than 96 input rows");
+  const int gx = (int)std::min<long long>((n + 255) / 256, 152LL * 8);
+  rowcomb_kernel<<<dim3(gx, (k + 15) / 16), 256, 0, s>>>(k, n, m, alpha, coef, ldc, In, beta, Out);
+  EA_LAUNCH();
+}
 
 // C[i][j] = sum_t A[i][t] B[j][t] for i < ma, j < mb (split over t)
 static void gram(cudaStream_t s, const double* A, int ma, const double* B, int mb, long long n, double* C,
                  long long ldc) {
   if (ma <= 0 || mb <= 0) return;
-  int nz = (int)std::min<long long>(std::max<long long>(1, n / 4096), 256);
-  long long chunk = (n + nz - 1) / nz;
+  int nz = (int)std::min<long long>(std::max<long long>(1, n / 8192), 128);
+  const long long chunk = (n + nz - 1) / nz;
   nz = (int)((n + chunk - 1) / chunk);
   DArr<double> P((size_t)nz * ma * mb, s);
-  fill(s, P.p, P.n, 0.0);
-  // full chunks through the batched GEMM, the tail separately
-  int nfull = (int)(n / chunk);
-  if (nfull > 0) {
-    GemmBatch bt;
-    bt.nb1 = nfull;
-    bt.sA1 = chunk;
-    bt.sB1 = chunk;
-    bt.sC1 = (long long)ma * mb;
-    dgemm(s, false, true, ma, mb, (int)chunk, 1.0, A, n, B, n, 0.0, P.p, mb, bt);
-  }
-  long long tail = n - (long long)nfull * chunk;
-  if (tail > 0)
-    dgemm(s, false, true, ma, mb, (int)tail, 1.0, A + nfull * chunk, n, B + nfull * chunk, n, 0.0,
-          P.p + (long long)nfull * ma * mb, mb);
-  int count = ma * mb;
+  gram_partial<<<dim3(nz, (ma + 7) / 8, (mb + 3) / 4), 256, 0, s>>>(A, ma, B, mb, n, chunk, P.p);
+  EA_LAUNCH();
+  const int count = ma * mb;
   reduce_partials<<<(count + 255) / 256, 256, 0, s>>>(P.p, nz, count, C, ma, mb, ldc);
   EA_LAUNCH();
 }
@@ -313,8 +385,8 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
     EA_LAUNCH();
     jacobi_eigh(s, m, Gs.p, w.p, U.p);
     // Ritz vectors and their sigma: X = U[:, :k]^T V
-    dgemm(s, true, false, k, (int)n, m, 1.0, U.p, m, V.p, n, 0.0, Xr.p, n);
-    dgemm(s, true, false, k, (int)n, m, 1.0, U.p, m, S.p, n, 0.0, SX.p, n);
+    rowcomb(s, k, n, m, 1.0, U.p, m, V.p, 0.0, Xr.p);
+    rowcomb(s, k, n, m, 1.0, U.p, m, S.p, 0.0, SX.p);
     residual_kernel<<<dim3(nb, k), 256, 0, s>>>(SX.p, Xr.p, w.p, R.p, n, k, part.p);
     EA_LAUNCH();
     finish_norms<<<1, 64, 0, s>>>(part.p, nb, k, rnd.p);
@@ -377,7 +449,7 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
     EA_LAUNCH();
     for (int pass = 0; pass < 2; ++pass) {
       gram(s, V.p, m, Dn.p, nn, n, C.p, nn);
-      dgemm(s, true, false, nn, (int)n, m, -1.0, C.p, nn, V.p, n, 1.0, Dn.p, n);
+      rowcomb(s, nn, n, m, -1.0, C.p, nn, V.p, 1.0, Dn.p);
     }
     gram(s, Dn.p, nn, Dn.p, nn, n, Gd.p, nn);
     symmetrize<<<1, 256, 0, s>>>(Gd.p, nn, nn, Zd.p);
@@ -394,15 +466,15 @@ static bool davidson_phase(cudaStream_t s, State& st, int k, int prec, const eaa
       int keep = std::min(std::max(2 * k, k), m);
       keep = std::min(keep, mmax - nacc);
       DArr<double> T((size_t)keep * n, s);
-      dgemm(s, true, false, keep, (int)n, m, 1.0, U.p, m, V.p, n, 0.0, T.p, n);
+      rowcomb(s, keep, n, m, 1.0, U.p, m, V.p, 0.0, T.p);
       EA_CK(cudaMemcpyAsync(V.p, T.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, s));
-      dgemm(s, true, false, keep, (int)n, m, 1.0, U.p, m, S.p, n, 0.0, T.p, n);
+      rowcomb(s, keep, n, m, 1.0, U.p, m, S.p, 0.0, T.p);
       EA_CK(cudaMemcpyAsync(S.p, T.p, sizeof(double) * keep * n, cudaMemcpyDeviceToDevice, s));
       m = keep;
       mg = 0;
     }
     // new orthonormal directions: coef^T Dn
-    dgemm(s, true, false, nacc, (int)n, nn, 1.0, coef.p, nn, Dn.p, n, 0.0, V.p + (long long)m * n, n);
+    rowcomb(s, nacc, n, nn, 1.0, coef.p, nn, Dn.p, 0.0, V.p + (long long)m * n);
     apply_sigma(s, st, prec, nacc, V.p + (long long)m * n, S.p + (long long)m * n);
     m += nacc;
   }
@@ -422,8 +494,8 @@ static void final_ritz(cudaStream_t s, State& st, int k, int prec, std::vector<d
   symmetrize<<<1, 256, 0, s>>>(G.p, k, k, Gs.p);
   EA_LAUNCH();
   jacobi_eigh(s, k, Gs.p, w.p, U.p);
-  dgemm(s, true, false, k, (int)n, k, 1.0, U.p, k, st.evecs.p, n, 0.0, X2.p, n);
-  dgemm(s, true, false, k, (int)n, k, 1.0, U.p, k, SX.p, n, 0.0, S2.p, n);
+  rowcomb(s, k, n, k, 1.0, U.p, k, st.evecs.p, 0.0, X2.p);
+  rowcomb(s, k, n, k, 1.0, U.p, k, SX.p, 0.0, S2.p);
   const int nb = std::min(256, (int)std::max<long long>(1, (n + 255) / 256));
   DArr<double> part((size_t)k * nb, s);
   residual_kernel<<<dim3(nb, k), 256, 0, s>>>(S2.p, X2.p, w.p, R.p, n, k, part.p);
