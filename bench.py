@@ -145,6 +145,14 @@ def cpu_baseline(pr, nvec=1):
             "sample": f"{nvec} sigma vector(s) of {WORKLOAD} (numpy FP64, BLAS on all host cores), {dt:.1f} s"}
 
 
+def bench_config(o, v, naux):
+    """The workload both arms report (the reference arm times one vector of it per step)."""
+    return {"workload": f"{WORKLOAD}: canonical EA-ADC(3), o={o}, v={v}, naux={naux}, {NROOTS} roots",
+            "nvec_per_step": NROOTS, "l2": "flushed (256 MB write) between timed steps",
+            "precision": "BF16 tensor-core operands, FP32 accumulation; DF coupling pieces FP32; "
+                         "diagonal and 1p/1p block FP64"}
+
+
 def golden_roots():
     p = os.path.join(ROOT, "tests", "golden", "canonical-200.npz")
     return np.load(p)["omega3"] if os.path.exists(p) else None
@@ -195,7 +203,7 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": fl / (val * 1e12) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"{WORKLOAD} (o={o}, v={v}, naux={naux})", "nvec": 1},
+            "data": "synthetic", "config": bench_config(o, v, naux),
             "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": "1 sigma vector per step (numpy FP64 oracle on all host cores)"},
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -317,10 +325,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: canonical EA-ADC(3), o={o}, v={v}, naux={naux}, {NROOTS} roots",
-                       "nvec_per_step": nvec, "l2": "flushed (256 MB write) between timed steps",
-                       "precision": "BF16 tensor-core operands, FP32 accumulation; DF coupling pieces FP32; "
-                                    "diagonal and 1p/1p block FP64"},
+            "config": bench_config(o, v, naux),
             "e2e": {"value": e2e_val, "unit": "TFLOP/s", "h2d_bytes_per_step": nvec * dim * 8,
                     "d2h_bytes_per_step": nvec * dim * 8},
             "gpu_launches": int(n1 - n0),
