@@ -145,6 +145,21 @@ def cpu_baseline(pr, nvec=1):
             "sample": f"{nvec} sigma vector(s) of {WORKLOAD} (numpy FP64, BLAS on all host cores), {dt:.1f} s"}
 
 
+def job_rate(local_ms, flops_per_rank_step, world, device):
+    """Whole-job rate of weak-scaled replicas: every rank does the same work
+    per step; the step time is the slowest rank's (max over ranks).  Returns
+    (ms_per_step, TFLOP/s of all ranks together)."""
+    ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * flops_per_rank_step / (ms * 1e-3) / 1e12
+
+
 def bench_config(o, v, naux):
     """The workload both arms report (the reference arm times one vector of it per step)."""
     return {"workload": f"{WORKLOAD}: canonical EA-ADC(3), o={o}, v={v}, naux={naux}, {NROOTS} roots",
@@ -309,12 +324,7 @@ def main():
                 t0 = time.perf_counter()
                 E.eaadc_sigma_host(ctx, 0, xn, E.EAADC_MIXED_BF16, out=yn)
                 e2e_t.append(time.perf_counter() - t0)
-        mean_ms = statistics.mean(ms)
-        if world > 1:
-            t = torch.tensor([mean_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            mean_ms = float(t.item())
-        value = world * fl_step / (mean_ms * 1e-3) / 1e12
+        mean_ms, value = job_rate(statistics.mean(ms), fl_step, world, "cuda")
         e2e_val = fl_step / statistics.mean(e2e_t) / 1e12
         bf16_peak, hbm_peak, src = peaks()
         achieved = ladder_flops(o, v, naux, nvec) / (lms * 1e-3) / 1e12
