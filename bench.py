@@ -168,6 +168,37 @@ def bench_config(o, v, naux):
                          "diagonal and 1p/1p block FP64"}
 
 
+FNO_STATES, FNO_THRESH, NAF_THRESH = 4, 0.15, 0.1
+
+
+def fno_states(E, ctx):
+    """Per-state truncated spaces (Sec. III) for the 4 lowest canonical ADC(2)
+    roots: build (canonical ADC(2) roots, densities, natural orbitals, NAFs,
+    intermediates), the 3 lowest roots of every state (BF16 Davidson with a
+    split-BF16 Ritz step) and Eq. 30 (FP64 ADC(2) in each truncated space).
+    Thresholds 0.15 (occupation) and 0.1 (auxiliary metric) keep about 60 %
+    of the virtuals and half of the auxiliary functions of this problem."""
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E.eaadc_build_states(ctx, FNO_STATES, FNO_THRESH, NAF_THRESH, 3, 1.0, can_opts=dict(tol=1e-6, maxit=300))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    om, rn, it, st = E.eaadc_davidson(ctx, 3, tol=1e-5, prec=E.EAADC_MIXED_BF16, refine=3, max_sub=40, maxit=300)
+    t2 = time.perf_counter()
+    en = E.eaadc_ea_energies(ctx, dict(tol=1e-6, maxit=300))
+    t3 = time.perf_counter()
+    info = [E.eaadc_state_info(ctx, k) for k in range(FNO_STATES)]
+    return {"nstates": FNO_STATES, "fno_thresh": FNO_THRESH, "naf_thresh": NAF_THRESH,
+            "vprime": [i[0] for i in info], "nauxprime": [i[1] for i in info],
+            "build_s": t1 - t0, "davidson_s": t2 - t1, "eq30_s": t3 - t2, "davidson_iterations": [int(i) for i in it],
+            "omega_uncorr_eh": [float(w) for w in en["omega_uncorr"]],
+            "omega_corr_eh": [float(w) for w in en["omega_corr"]],
+            "omega2_can_eh": [float(w) for w in en["omega2_can"]],
+            "mode": "states sequential; BF16 Davidson + split-BF16 Ritz step per state; Eq. 30 in FP64"}
+
+
 def golden_roots():
     p = os.path.join(ROOT, "tests", "golden", "canonical-200.npz")
     return np.load(p)["omega3"] if os.path.exists(p) else None
@@ -233,6 +264,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-roots", action="store_true", help="skip the time-to-roots solves")
     ap.add_argument("--no-fp64-baseline", action="store_true", help="skip the FP64 GPU Davidson baseline")
+    ap.add_argument("--no-fno", action="store_true", help="skip the per-state FNO/NAF run")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -349,6 +381,8 @@ def main():
         }
         if roots is not None:
             line["time_to_roots"] = roots
+        if not args.no_fno and rank == 0:
+            line["fno_states"] = fno_states(E, ctx)
         if rank == 0 and world == 1:
             line["cpu_baseline"] = cpu_baseline(pr, 1)
         if rank == 0:

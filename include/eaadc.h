@@ -211,7 +211,8 @@ eaadc_status eaadc_build_states(eaadc_ctx* ctx, int nstates, const double* fno_t
  * omega^(3)_FNO the target root of the last eaadc_davidson, omega^(2)_FNO the
  * target root of EA-ADC(2) solved here in the same truncated space (FP64
  * Davidson with opts, defaults as for eaadc_build_states; as many roots as the
- * last eaadc_davidson).  Attachment energies in hartree (EA = -omega).
+ * last eaadc_davidson, and at least k + 2 for state k, whose canonical root is
+ * the (k+1)-th).  Attachment energies in hartree (EA = -omega).
  * Each output is host [nstates] and may be NULL. */
 eaadc_status eaadc_ea_energies(eaadc_ctx* ctx, const eaadc_davidson_opts* opts, double* omega_uncorr,
                                double* omega_corr, double* omega2_can, double* omega2_fno);

@@ -217,7 +217,8 @@ void ea_energies(eaadc_ctx* ctx, const eaadc_davidson_opts& opts, double* w_unco
     copy_d(s, t.Bov, st.Bov.p, st.Bov.n);
     copy_d(s, t.Bvv, st.Bvv.p, st.Bvv.n);
     build_state_intermediates(ctx, t);
-    const int nr = (int)st.omega.size();
+    // state si comes from the si-th canonical ADC(2) root: solve past it
+    const int nr = std::max((int)st.omega.size(), (int)si + 2);
     std::vector<double> w2(nr);
     if (!davidson_state(s, t, nr, opts, w2.data(), nullptr, nullptr))
       fail(EAADC_ERR_NOCONV, "EA-ADC(2) roots of state " + std::to_string(si) + " did not converge");
