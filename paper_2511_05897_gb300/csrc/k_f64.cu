@@ -242,9 +242,104 @@ void sgemm_t(cudaStream_t s, int M, int N, int K, float alpha, const float* A, l
   EA_LAUNCH();
 }
 
+// Skinny products (N <= 8 columns), bandwidth-bound: every element of A is
+// read once.  TA = false (A row-major M x K): one warp per row of C, lanes
+// stride over K.  TA = true (A stored K x M): one thread per column of A
+// (coalesced over m), K split over blockIdx.y into partial panels.
+template <class T, bool TB>
+__global__ void skinny_rows(int M, int N, int K, T alpha, const T* __restrict__ A, long long lda,
+                            const T* __restrict__ B, long long ldb, T beta, T* __restrict__ C, long long ldc) {
+  extern __shared__ unsigned char skinny_smem[];
+  T* Bs = reinterpret_cast<T*>(skinny_smem);  // [K][8], zero beyond N
+  for (int e = threadIdx.x; e < K * 8; e += blockDim.x) {
+    const int k = e >> 3, n = e & 7;
+    Bs[e] = n < N ? (TB ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]) : T(0);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long wpb = blockDim.x >> 5;
+  for (long long m = blockIdx.x * wpb + (threadIdx.x >> 5); m < M; m += (long long)gridDim.x * wpb) {
+    T acc[8];
+#pragma unroll
+    for (int n = 0; n < 8; ++n) acc[n] = T(0);
+    const T* a = A + m * lda;
+#pragma unroll 4
+    for (int k = lane; k < K; k += 32) {
+      const T x = a[k];
+      const T* bk = Bs + k * 8;
+#pragma unroll
+      for (int n = 0; n < 8; ++n) acc[n] += x * bk[n];
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+      for (int o = 16; o; o >>= 1) acc[n] += __shfl_xor_sync(0xffffffffu, acc[n], o);
+    if (lane == 0)
+      for (int n = 0; n < N; ++n) {
+        T* c = C + m * ldc + n;
+        *c = beta == T(0) ? alpha * acc[n] : alpha * acc[n] + beta * *c;
+      }
+  }
+}
+
+template <class T, bool TB>
+__global__ void skinny_cols(int M, int N, int K, const T* __restrict__ A, long long lda, const T* __restrict__ B,
+                            long long ldb, int kchunk, T* __restrict__ P) {
+  extern __shared__ unsigned char skinny_smem[];
+  T* Bs = reinterpret_cast<T*>(skinny_smem);  // [kchunk][8], zero beyond N
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
+  for (int e = threadIdx.x; e < (k1 - k0) * 8; e += blockDim.x) {
+    const int k = k0 + (e >> 3), n = e & 7;
+    Bs[e] = n < N ? (TB ? B[(long long)n * ldb + k] : B[(long long)k * ldb + n]) : T(0);
+  }
+  __syncthreads();
+  if (m >= M) return;
+  T acc[8];
+#pragma unroll
+  for (int n = 0; n < 8; ++n) acc[n] = T(0);
+#pragma unroll 8
+  for (int k = k0; k < k1; ++k) {
+    const T x = A[(long long)k * lda + m];
+    const T* bk = Bs + (k - k0) * 8;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) acc[n] += x * bk[n];
+  }
+  T* out = P + (long long)blockIdx.y * M * N + (long long)m * N;
+  for (int n = 0; n < N; ++n) out[n] = acc[n];
+}
+
+template <class T, bool TA, bool TB>
+void skinny_t(cudaStream_t s, int M, int N, int K, T alpha, const T* A, long long lda, const T* B, long long ldb,
+              T beta, T* C, long long ldc) {
+  if (!TA) {
+    const int grid = (int)std::min<long long>(((long long)M + 7) / 8, 152LL * 16);
+    skinny_rows<T, TB><<<grid, 256, (size_t)K * 8 * sizeof(T), s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    EA_LAUNCH();
+    return;
+  }
+  const int bx = (M + 255) / 256;
+  int ks = (int)std::max<long long>(1, std::min<long long>((608 + bx - 1) / bx, (K + 255) / 256));
+  ks = std::max(ks, (K + 511) / 512);  // staged B slice <= 512 x 8 elements (32 KB in FP64)
+  const int kchunk = (K + ks - 1) / ks;
+  ks = (K + kchunk - 1) / kchunk;
+  const long long panel = (long long)M * N;
+  DArr<T> P((size_t)(panel * ks), s);
+  skinny_cols<T, TB><<<dim3(bx, ks), 256, (size_t)kchunk * 8 * sizeof(T), s>>>(M, N, K, A, lda, B, ldb, kchunk,
+                                                                                  P.p);
+  EA_LAUNCH();
+  // C = alpha * sum of panels + beta * C (splitk_reduce adds beta * C)
+  if (alpha != T(1)) fail(EAADC_ERR_ARG, "skinny gemm: alpha != 1 with a transposed A");
+  splitk_reduce<<<(int)std::min<long long>((panel + 255) / 256, 4096), 256, 0, s>>>(P.p, ks, panel, M, N, beta, C, ldc);
+  EA_LAUNCH();
+}
+
 template <class T, bool TA, bool TB>
 void dgemm_t(cudaStream_t s, int M, int N, int K, T alpha, const T* A, long long lda,
              const T* B, long long ldb, T beta, T* C, long long ldc, const GemmBatch& bt) {
+  if (bt.nb1 * bt.nb2 == 1 && N <= 8 && K >= 64 && (TA ? alpha == T(1) : (long long)K * 8 * sizeof(T) <= 48 * 1024)) {
+    skinny_t<T, TA, TB>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    return;
+  }
   if constexpr (std::is_same<T, float>::value) {
     sgemm_t<TA, TB>(s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bt);
     return;
