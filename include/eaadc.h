@@ -122,6 +122,11 @@ eaadc_status eaadc_state_info(const eaadc_ctx* ctx, int state, int* vprime, int*
 eaadc_status eaadc_sigma(eaadc_ctx* ctx, int state, int nvec, const double* x_dev,
                          double* sigma_dev, int prec, void* stream);
 
+/* In the reduced-precision modes, the first call for a given (state size,
+ * nvec) shape also times the candidate chunk sizes of the ladder (each run
+ * computes the full result) and keeps the fastest for later calls; that
+ * first call waits for the stream.  The same holds for eaadc_ladder. */
+
 /* Same as eaadc_sigma with host buffers [nvec][dim]; includes the copies. */
 eaadc_status eaadc_sigma_host(eaadc_ctx* ctx, int state, int nvec, const double* x_host,
                               double* sigma_host, int prec);

@@ -27,6 +27,10 @@
 #include "tc_gemm2.cuh"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 namespace ea {
 namespace {
@@ -408,16 +412,68 @@ __global__ void compact_f32(const float* __restrict__ in, long long ip, float* _
 // Z rows hold qc blocks of pad8(v) columns (pads zero, matching the zero pads
 // of the b-major copy of B); chunks accumulate by TMA reduce-add.  In split
 // mode Z is formed in FP32 by the three split products and split again.
+// ladder_run computes it in chunks of qc auxiliary functions.
+static void ladder_run(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out, long long op,
+                       int qc);
+
+// Ladder chunk size (auxiliary functions per stage-1/stage-2 pair), tuned
+// once per shape: the intermediate Z of one chunk should stay in L2 between
+// the two stages, but larger chunks mean fewer launches and longer GEMMs.
+// The first call for a (v, naux, nmat, split) shape times the candidate
+// chunk sizes (Z of 12, 24, 48 and 96 M elements) with CUDA events on the
+// stream, each producing the full ladder in out, and keeps the fastest.
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, bool>, int> g_ladder_qc;
+
 void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out, long long op) {
+  const int v = st.v, naux = st.naux;
+  const bool x3 = Wlo != nullptr;
+  const long long per_q = std::max<long long>(1, (long long)nmat * v * pad8(v));
+  auto qc_of = [&](long long budget) { return (int)std::min<long long>(naux, std::max<long long>(1, budget / per_q)); };
+  const auto key = std::make_tuple(v, naux, nmat, x3);
+  int qc = -1;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_ladder_qc.find(key);
+    if (it != g_ladder_qc.end()) qc = it->second;
+  }
+  if (qc < 0) {
+    std::vector<int> cand;
+    for (long long b : {12LL << 20, 24LL << 20, 48LL << 20, 96LL << 20}) {
+      const int q = qc_of(x3 ? b / 2 : b);
+      if (std::find(cand.begin(), cand.end(), q) == cand.end()) cand.push_back(q);
+    }
+    qc = cand.back();
+    if (cand.size() > 1) {
+      cudaEvent_t e0, e1;
+      EA_CK(cudaEventCreate(&e0));
+      EA_CK(cudaEventCreate(&e1));
+      float best = 1e30f;
+      for (int q : cand) {
+        ladder_run(s, st, Wbf, Wlo, nmat, out, op, q);  // warm-up (and the allocation of Z)
+        EA_CK(cudaEventRecord(e0, s));
+        ladder_run(s, st, Wbf, Wlo, nmat, out, op, q);
+        EA_CK(cudaEventRecord(e1, s));
+        EA_CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        EA_CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; qc = q; }
+      }
+      EA_CK(cudaEventDestroy(e0));
+      EA_CK(cudaEventDestroy(e1));
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_ladder_qc[key] = qc;
+  }
+  ladder_run(s, st, Wbf, Wlo, nmat, out, op, qc);
+}
+
+static void ladder_run(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out, long long op,
+                       int qc) {
   const int v = st.v, naux = st.naux;
   const bool x3 = Wlo != nullptr;
   const long long dp = pad8(v), wp = rp64(v), bk = (long long)naux * dp;
   const long long bvp = st.bvv_pitch, bbp = st.bb_pitch;
-  // chunk of auxiliary functions: Z about 48M (split mode 24M) elements, so
-  // that it stays in L2 between the two stages
-  const long long budget = x3 ? (24LL << 20) : (48LL << 20);
-  int qc = (int)std::max<long long>(1, budget / std::max<long long>(1, (long long)nmat * v * dp));
-  qc = std::min(qc, naux);
   const long long zp = rp64((long long)qc * dp);  // Z row pitch
   const size_t zn = (size_t)nmat * v * zp;
   DArr<bf16> Z(zn, s), Zl;
