@@ -329,11 +329,13 @@ def main():
             # dominant kernel: the DF ladder alone, same stream
             lev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                    for _ in range(args.steps)]
+            torch.cuda.nvtx.range_push("roofline_ladder")  # lets a profiler select these launches
             for i in range(args.steps):
                 flush.zero_()
                 lev[i][0].record(stream)
                 E.eaadc_ladder(ctx, 0, nvec, x.data_ptr(), lad.data_ptr(), sh)
                 lev[i][1].record(stream)
+            torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
             lms = statistics.mean(a.elapsed_time(b) for a, b in lev)
             # the split-BF16 (three-product) sigma, same workload (after an untimed

@@ -413,17 +413,25 @@ __global__ void compact_f32(const float* __restrict__ in, long long ip, float* _
 // of the b-major copy of B); chunks accumulate by TMA reduce-add.  In split
 // mode Z is formed in FP32 by the three split products and split again.
 // ladder_run computes it in chunks of qc auxiliary functions.
+struct LadderPlan {
+  int qc;      // auxiliary functions per chunk
+  int var1;    // tc_gemm2 pipeline variant of stage 1 (0: by K)
+  int var2;    // ... of stage 2
+};
 static void ladder_run(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out, long long op,
-                       int qc);
+                       const LadderPlan& plan);
 
-// Ladder chunk size (auxiliary functions per stage-1/stage-2 pair), tuned
+// Ladder plan (chunk size and the GEMM pipeline shape of each stage), tuned
 // once per shape: the intermediate Z of one chunk should stay in L2 between
-// the two stages, but larger chunks mean fewer launches and longer GEMMs.
+// the two stages, but larger chunks mean fewer launches and longer GEMMs;
+// short-K stage 1 and long-K stage 2 want different load / epilogue depths.
 // The first call for a (v, naux, nmat, split) shape times the candidate
-// chunk sizes (Z of 12, 24, 48 and 96 M elements) with CUDA events on the
-// stream, each producing the full ladder in out, and keeps the fastest.
+// chunk sizes (Z of 12, 24, 48 and 96 M elements) with the default pipelines,
+// then the pipeline variants of each stage at the best chunk size, with CUDA
+// events on the stream (every run producing the full ladder in out), and
+// keeps the fastest plan.
 static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int, bool>, int> g_ladder_qc;
+static std::map<std::tuple<int, int, int, bool>, LadderPlan> g_ladder_plan;
 
 void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out, long long op) {
   const int v = st.v, naux = st.naux;
@@ -431,46 +439,58 @@ void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int 
   const long long per_q = std::max<long long>(1, (long long)nmat * v * pad8(v));
   auto qc_of = [&](long long budget) { return (int)std::min<long long>(naux, std::max<long long>(1, budget / per_q)); };
   const auto key = std::make_tuple(v, naux, nmat, x3);
-  int qc = -1;
+  LadderPlan plan{-1, 0, 0};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_ladder_qc.find(key);
-    if (it != g_ladder_qc.end()) qc = it->second;
+    auto it = g_ladder_plan.find(key);
+    if (it != g_ladder_plan.end()) plan = it->second;
   }
-  if (qc < 0) {
+  if (plan.qc < 0) {
     std::vector<int> cand;
     for (long long b : {12LL << 20, 24LL << 20, 48LL << 20, 96LL << 20}) {
       const int q = qc_of(x3 ? b / 2 : b);
       if (std::find(cand.begin(), cand.end(), q) == cand.end()) cand.push_back(q);
     }
-    qc = cand.back();
+    plan = LadderPlan{cand.back(), 0, 0};
     if (cand.size() > 1) {
       cudaEvent_t e0, e1;
       EA_CK(cudaEventCreate(&e0));
       EA_CK(cudaEventCreate(&e1));
-      float best = 1e30f;
-      for (int q : cand) {
-        ladder_run(s, st, Wbf, Wlo, nmat, out, op, q);  // warm-up (and the allocation of Z)
+      auto time_plan = [&](const LadderPlan& p) {
+        ladder_run(s, st, Wbf, Wlo, nmat, out, op, p);  // warm-up (and the allocation of Z)
         EA_CK(cudaEventRecord(e0, s));
-        ladder_run(s, st, Wbf, Wlo, nmat, out, op, q);
+        ladder_run(s, st, Wbf, Wlo, nmat, out, op, p);
         EA_CK(cudaEventRecord(e1, s));
         EA_CK(cudaEventSynchronize(e1));
         float ms = 0.f;
         EA_CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; qc = q; }
+        return ms;
+      };
+      float best = 1e30f;
+      for (int q : cand) {
+        const float ms = time_plan(LadderPlan{q, 0, 0});
+        if (ms < best) { best = ms; plan = LadderPlan{q, 0, 0}; }
       }
+      const bool fits43 = tc2::smem_bytes(pick_bn(v), 4, 3) <= 232448;
+      for (int v1 : {1, 2, 3})
+        for (int v2 : {1, 2, 3}) {
+          if (!fits43 && (v1 == 3 || v2 == 3)) continue;
+          const LadderPlan p{plan.qc, v1, v2};
+          const float ms = time_plan(p);
+          if (ms < best) { best = ms; plan = p; }
+        }
       EA_CK(cudaEventDestroy(e0));
       EA_CK(cudaEventDestroy(e1));
     }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_ladder_qc[key] = qc;
+    g_ladder_plan[key] = plan;
   }
-  ladder_run(s, st, Wbf, Wlo, nmat, out, op, qc);
+  ladder_run(s, st, Wbf, Wlo, nmat, out, op, plan);
 }
 
 static void ladder_run(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out, long long op,
-                       int qc) {
-  const int v = st.v, naux = st.naux;
+                       const LadderPlan& plan) {
+  const int v = st.v, naux = st.naux, qc = plan.qc;
   const bool x3 = Wlo != nullptr;
   const long long dp = pad8(v), wp = rp64(v), bk = (long long)naux * dp;
   const long long bvp = st.bvv_pitch, bbp = st.bb_pitch;
@@ -502,6 +522,7 @@ static void ladder_run(cudaStream_t s, State& st, const bf16* Wbf, const bf16* W
     g1.nzlo = q; g1.nz = q * nmat;
     g1.a_sel = tc2::Z_LO; g1.a_z0 = Q0;
     g1.b_sel = tc2::Z_HI;
+    g1.variant = plan.var1;
     if (!x3) {
       TmaMap mZo = make_tma_out4d(Z.p, 2, v, q, v, nmat, dp, zp, (long long)v * zp);
       g1.out_bf16 = 1;
@@ -517,6 +538,7 @@ static void ladder_run(cudaStream_t s, State& st, const bf16* Wbf, const bf16* W
     tc2::Args g2 = gargs(nmat * v, v, (int)(q * dp), st.err.p);
     g2.b_k0 = (int)(Q0 * dp);
     g2.reduce = (Q0 > 0);
+    g2.variant = plan.var2;
     if (!x3) {
       tc_gemm2(s, mZ, mBb, mOut, g2);
     } else {

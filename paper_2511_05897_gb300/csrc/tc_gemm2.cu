@@ -61,10 +61,13 @@ int pick_bn(int N) {
 namespace {
 template <int kS, int kEB>
 void launch_variant(cudaStream_t s, const TmaMap& A, const TmaMap& B, const TmaMap& C, const tc2::Args& a, int grid) {
+  constexpr size_t kMaxSmem = 232448;  // per-block opt-in limit
+  if (tc2::smem_bytes(a.BN, kS, kEB) > kMaxSmem)
+    fail(EAADC_ERR_ARG, "tc_gemm2: pipeline variant does not fit shared memory at this tile width");
   static bool attr = false;  // opt in to the largest shared-memory size once per variant
   if (!attr) {
     EA_CK(cudaFuncSetAttribute(tc2::gemm_persistent<kS, kEB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)tc2::smem_bytes(256, kS, kEB)));
+                               (int)std::min(tc2::smem_bytes(256, kS, kEB), kMaxSmem)));
     attr = true;
   }
   tc2::gemm_persistent<kS, kEB><<<grid, tc2::kThreads, tc2::smem_bytes(a.BN, kS, kEB), s>>>(A.map, B.map, C.map, a);
@@ -84,8 +87,11 @@ void tc_gemm2(cudaStream_t s, const TmaMap& A, const TmaMap& B, const TmaMap& C,
   if (tiles > (1LL << 31) - 1) fail(EAADC_ERR_ARG, "tc_gemm2: too many tiles");
   const int grid = (int)std::min<long long>(tiles, sm_count());
   const int nk = (a.K + tc2::kBK - 1) / tc2::kBK;
-  if (nk >= 8) launch_variant<4, 2>(s, A, B, C, a, grid);  // long K: bytes in flight
-  else launch_variant<3, 4>(s, A, B, C, a, grid);          // short K: epilogue depth
+  const int var = a.variant ? a.variant : (nk >= 8 ? 1 : 2);
+  if (var == 1) launch_variant<4, 2>(s, A, B, C, a, grid);       // long K: bytes in flight
+  else if (var == 2) launch_variant<3, 4>(s, A, B, C, a, grid);  // short K: epilogue depth
+  else if (var == 3) launch_variant<4, 3>(s, A, B, C, a, grid);
+  else fail(EAADC_ERR_ARG, "tc_gemm2: unknown variant");
 }
 
 }  // namespace ea

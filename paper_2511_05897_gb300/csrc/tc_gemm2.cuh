@@ -37,6 +37,8 @@ struct Args {
   int reduce;          // 1: C += result (TMA reduce-add), 0: C = result
   int out_bf16;        // output element type: 0 fp32, 1 bf16
   int* err;
+  int variant;         // pipeline shape: 0 by K (see tc_gemm2), 1 <4 stages, 2 staging buffers>,
+                       // 2 <3, 4>, 3 <4, 3>
 };
 
 constexpr int kBM = 128, kBK = 64, kEpiWarps = 4;
