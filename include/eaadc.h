@@ -240,7 +240,8 @@ eaadc_status eaadc_eigh_sym(int n, const double* a_dev, double* w_dev, double* v
  *   m = w4 . h3 + b4   (width 256, FP32 on the device)
  * with the 16 features f_I (rr_I sqrt(dim), asinh(D_I - theta),
  * clip(1/(theta - D_I), +-100)/100, eps_k, asinh(eps_b) (1p: asinh(eps_a)),
- * asinh(eps_c), theta, log10 ||r||, [1p], [2p1h with b = c], 6 zeros).
+ * asinh(eps_c), theta, log10 ||r||, [1p], [2p1h with b = c], (bb|cc) = the
+ * ladder diagonal for 2p1h, 5 zeros).
  * Weights: EAADC_MLP_PARAMS floats, W1[256][16] b1[256] W2[256][256] b2
  * W3[256][256] b3 w4[256] b4[1].  Training minimises the mean over vectors of
  * 1 - cos^2(delta, t), t = (I - y y^T)(y* - y) the exact correction of the

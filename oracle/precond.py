@@ -72,8 +72,15 @@ def element_energies(o, v, eo, ev):
     return ek, eb, ec, one, dg
 
 
-def features(r, D, theta, o, v, eo, ev):
-    """Feature matrix [dim, 16], normalised residual rr and diagonal term rr/(theta - D)."""
+def ladder_diagonal(Bvv):
+    """(bb|cc) = sum_Q B^Q_bb B^Q_cc, [v, v]."""
+    d = np.einsum("Qbb->Qb", Bvv)
+    return d.T @ d
+
+
+def features(r, D, theta, o, v, eo, ev, lad=None):
+    """Feature matrix [dim, 16], normalised residual rr and diagonal term
+    rr/(theta - D); lad = ladder_diagonal(B_vv) (zeros when None)."""
     dim = v + o * v * v
     rn = np.linalg.norm(r)
     rr = r / rn
@@ -90,6 +97,8 @@ def features(r, D, theta, o, v, eo, ev):
     f[:, 7] = np.log10(rn)
     f[:, 8] = one
     f[:, 9] = dg
+    if lad is not None:
+        f[v:, 10] = np.broadcast_to(lad, (o, v, v)).ravel()
     return f, rr, rr / den
 
 

@@ -163,6 +163,7 @@ struct State {
   DArr<double> trX, trR;
   std::vector<double> trTheta;
   int trN = 0, trK = 0;
+  DArr<double> lad_diag;                       // (bb|cc) [v'][v'], a feature of the learned correction
   long long bvv_pitch = 0, bb_pitch = 0;      // row pitches (elements) of Bvv_bf and Bb_bf
   DArr<int> err;                              // device error word of bounded waits
   bool mixed_ready = false;
@@ -185,9 +186,9 @@ struct Mlp {
 void mlp_forward(cudaStream_t s, const Mlp& net, long long n, const float* feat, float* m);
 // Features, normalised residual rr and diagonal term base = rr / (theta - D)
 // of nvec residual vectors R (rows of length st.dim) with Ritz values theta.
-void precond_features(cudaStream_t s, const State& st, int nvec, const double* R, const double* theta_dev,
+void precond_features(cudaStream_t s, State& st, int nvec, const double* R, const double* theta_dev,
                       const double* rnorm_dev, float* feat, float* rr, float* base);
-void precond_pairs(cudaStream_t s, const State& st, int nvec, const double* Y, const double* R,
+void precond_pairs(cudaStream_t s, State& st, int nvec, const double* Y, const double* R,
                    const double* theta_host, const double* Ys, float* feat, float* rr, float* base, float* T);
 double mlp_loss_grad(cudaStream_t s, Mlp& net, int nseg, const int* segs_host, const float* feat, const float* rr,
                      const float* base, const float* T, float lr, bool update);

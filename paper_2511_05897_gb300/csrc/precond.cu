@@ -7,6 +7,7 @@
 //   f0 rr_I sqrt(dim)      f1 asinh(D_I - theta)   f2 clip(1/(theta-D_I), +-100)/100
 //   f3 eps_k (2p1h)        f4 asinh(eps_b) (1p: asinh(eps_a))  f5 asinh(eps_c) (2p1h)
 //   f6 theta               f7 log10 ||r||          f8 [1p]   f9 [2p1h with b = c]
+//   f10 (bb|cc) for 2p1h (the ladder diagonal, absent from D)
 // (zero padding to 16).  The layers are FP32 GEMMs on CUDA cores; training
 // minimises the mean over vectors of 1 - cos^2(delta, t) against the projected
 // exact correction t = (I - y y^T)(y* - y), by backpropagation and Adam.
@@ -31,8 +32,8 @@ __device__ __forceinline__ double guard(double den) {
 __global__ void features_kernel(const double* __restrict__ R, long long dim, int o, int v,
                                 const double* __restrict__ D, const double* __restrict__ eo,
                                 const double* __restrict__ ev, const double* __restrict__ theta,
-                                const double* __restrict__ rnorm, int nvec, float* __restrict__ feat,
-                                float* __restrict__ rr, float* __restrict__ base) {
+                                const double* __restrict__ rnorm, const double* __restrict__ lad, int nvec,
+                                float* __restrict__ feat, float* __restrict__ rr, float* __restrict__ base) {
   const long long total = dim * nvec;
   const double sq = sqrt((double)dim);
   const long long vv = (long long)v * v;
@@ -42,7 +43,7 @@ __global__ void features_kernel(const double* __restrict__ R, long long dim, int
     const double th = theta[n], rn = rnorm[n];
     const double x = R[e] / rn;
     const double den = guard(th - D[i]);
-    double ek = 0.0, eb, ec = 0.0, one = 0.0, dg = 0.0;
+    double ek = 0.0, eb, ec = 0.0, one = 0.0, dg = 0.0, ld = 0.0;
     if (i < v) {
       eb = asinh(ev[i]);
       one = 1.0;
@@ -53,6 +54,7 @@ __global__ void features_kernel(const double* __restrict__ R, long long dim, int
       eb = asinh(ev[b]);
       ec = asinh(ev[c]);
       dg = (b == c) ? 1.0 : 0.0;
+      ld = lad[(long long)b * v + c];
     }
     float* f = feat + e * kMlpF;
     f[0] = (float)(x * sq);
@@ -65,8 +67,9 @@ __global__ void features_kernel(const double* __restrict__ R, long long dim, int
     f[7] = (float)log10(rn);
     f[8] = (float)one;
     f[9] = (float)dg;
+    f[10] = (float)ld;
 #pragma unroll
-    for (int q = 10; q < kMlpF; ++q) f[q] = 0.f;
+    for (int q = 11; q < kMlpF; ++q) f[q] = 0.f;
     rr[e] = (float)x;
     base[e] = (float)(x / den);
   }
@@ -279,10 +282,26 @@ void mlp_forward(cudaStream_t s, const Mlp& net, long long n, const float* feat,
   EA_CK(cudaMemcpyAsync(m, a.m.p, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
 }
 
-void precond_features(cudaStream_t s, const State& st, int nvec, const double* R, const double* theta_dev,
+// dq[Q][b] = B^Q_bb
+__global__ void bvv_diag(const double* __restrict__ Bvv, int naux, int v, double* __restrict__ dq) {
+  const long long total = (long long)naux * v;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long Q = e / v, b = e % v;
+    dq[e] = Bvv[(Q * v + b) * v + b];
+  }
+}
+
+void precond_features(cudaStream_t s, State& st, int nvec, const double* R, const double* theta_dev,
                       const double* rnorm_dev, float* feat, float* rr, float* base) {
+  if (!st.lad_diag.p) {  // (bb|cc) = sum_Q B^Q_bb B^Q_cc, once per state
+    DArr<double> dq((size_t)st.naux * st.v, s);
+    bvv_diag<<<gridn((long long)st.naux * st.v), 256, 0, s>>>(st.Bvv.p, st.naux, st.v, dq.p);
+    EA_LAUNCH();
+    st.lad_diag.alloc((size_t)st.v * st.v, s);
+    dgemm(s, true, false, st.v, st.v, st.naux, 1.0, dq.p, st.v, dq.p, st.v, 0.0, st.lad_diag.p, st.v);
+  }
   features_kernel<<<gridn(st.dim * nvec), 256, 0, s>>>(R, st.dim, st.o, st.v, st.diag.p, st.eo.p, st.ev.p, theta_dev,
-                                                       rnorm_dev, nvec, feat, rr, base);
+                                                       rnorm_dev, st.lad_diag.p, nvec, feat, rr, base);
   EA_LAUNCH();
 }
 
@@ -361,7 +380,7 @@ void mlp_load(cudaStream_t s, Mlp& net, const float* host) {
 
 // Training pairs of nvec Ritz vectors Y with residuals R and values theta;
 // Ys (optional) the converged eigenvectors of the same roots.
-void precond_pairs(cudaStream_t s, const State& st, int nvec, const double* Y, const double* R,
+void precond_pairs(cudaStream_t s, State& st, int nvec, const double* Y, const double* R,
                    const double* theta_host, const double* Ys, float* feat, float* rr, float* base, float* T) {
   const long long dim = st.dim;
   DArr<double> sums((size_t)3 * nvec, s), rn((size_t)nvec, s), th((size_t)nvec, s);

@@ -74,7 +74,7 @@ def test_pairs_and_forward_match_oracle(E):
         f, a, b, t = _pairs(E, ctx, X[t_it], Rs[t_it], th[t_it], Ys)
         dim = D.size
         for r in range(3):
-            Fo, rro, baseo = P.features(Rs[t_it, r], D, th[t_it, r], o, v, p.eo, p.ev)
+            Fo, rro, baseo = P.features(Rs[t_it, r], D, th[t_it, r], o, v, p.eo, p.ev, P.ladder_diagonal(p.Bvv))
             sl = slice(r * dim, (r + 1) * dim)
             assert np.allclose(f[sl].cpu().numpy(), Fo, rtol=2e-7, atol=2e-7 * np.abs(Fo).max())
             assert np.allclose(a[sl].cpu().numpy(), rro, rtol=2e-7, atol=1e-12)

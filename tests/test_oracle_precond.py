@@ -61,7 +61,7 @@ def test_zero_output_layer_is_the_diagonal_correction():
     r = np.random.default_rng(0).standard_normal(dim)
     theta = D.min() + 0.01
     D[3] = theta + 1e-12  # the guarded denominator
-    F, rr, base = P.features(r, D, theta, p.o, p.v, p.eo, p.ev)
+    F, rr, base = P.features(r, D, theta, p.o, p.v, p.eo, p.ev, P.ladder_diagonal(p.Bvv))
     net = _params(5)
     net["w4"][:] = 0.0
     net["b4"][:] = 0.0
@@ -77,6 +77,22 @@ def test_zero_output_layer_is_the_diagonal_correction():
     assert F[i, 3] == p.eo[k] and F[i, 4] == np.arcsinh(p.ev[b]) and F[i, 5] == np.arcsinh(p.ev[c])
     assert F[:p.v, 8].sum() == p.v and F[p.v:, 8].sum() == 0
     assert F[:, 9].sum() == p.o * p.v
+
+
+def test_ladder_feature_is_the_ladder_diagonal():
+    """Feature 10 of element (k, b, c) is the ladder's response to the unit
+    vector at (k, b, c), read at (k, b, c)."""
+    pr = make_problem(2, 4, 7, 3.0, 6)
+    p = R.Problem(pr["eps_occ"], pr["eps_vir"], pr["B"])
+    lad = P.ladder_diagonal(p.Bvv)
+    dim = p.v + p.o * p.v * p.v
+    F, _, _ = P.features(np.ones(dim), np.zeros(dim), -1.0, p.o, p.v, p.eo, p.ev, lad)
+    for k, b, c in [(0, 0, 0), (1, 2, 3), (0, 3, 1)]:
+        w = np.zeros((p.o, p.v, p.v))
+        w[k, b, c] = 1.0
+        resp = R.ladder_w(p, w)[k, b, c]
+        assert abs(F[p.v + (k * p.v + b) * p.v + c, 10] - resp) < 1e-14
+    assert not F[:p.v, 10].any()
 
 
 def test_loss_closed_forms():
