@@ -199,6 +199,36 @@ def fno_states(E, ctx):
             "mode": "states sequential; BF16 Davidson + split-BF16 Ritz step per state; Eq. 30 in FP64"}
 
 
+def end_to_end(E, pr, device, stream, fp64_build_s, fp64_solve_s):
+    """From host inputs to the 4 roots within 1e-5 Eh: upload, build (amplitude
+    ladder on the tensor cores, split BF16), BF16 Davidson with a split-BF16
+    Ritz step; against the FP64 upload + build + FP64 GPU Davidson."""
+    import torch
+
+    gold = golden_roots()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = E.eaadc_init(pr["o"], pr["v"], pr["naux"], pr["eps_occ"], pr["eps_vir"], pr["B"], device, stream)
+    try:
+        E.eaadc_set_build_precision(ctx, E.EAADC_MIXED_BF16X3)
+        E.eaadc_build_canonical(ctx, 3, 1.0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        om, rn, it, st = E.eaadc_davidson(ctx, NROOTS, tol=1e-5, prec=E.EAADC_MIXED_BF16, refine=3, max_sub=40,
+                                          maxit=300)
+        t2 = time.perf_counter()
+    finally:
+        E.eaadc_destroy(ctx)
+    out = {"ours": {"seconds": t2 - t0, "init_build_s": t1 - t0, "solve_s": t2 - t1,
+                    "mode": "split-BF16 amplitude ladder in the build; BF16 Davidson + split-BF16 Ritz step"},
+           "fp64_gpu": {"seconds": fp64_build_s + fp64_solve_s, "init_build_s": fp64_build_s,
+                        "solve_s": fp64_solve_s}}
+    if gold is not None:
+        out["ours"]["max_err_vs_oracle_eh"] = float(np.abs(om[0] - gold).max())
+    out["speedup_vs_fp64_gpu"] = out["fp64_gpu"]["seconds"] / out["ours"]["seconds"]
+    return out
+
+
 def golden_roots():
     p = os.path.join(ROOT, "tests", "golden", "canonical-200.npz")
     return np.load(p)["omega3"] if os.path.exists(p) else None
@@ -292,9 +322,13 @@ def main():
     o, v, naux = pr["o"], pr["v"], pr["naux"]
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
+    torch.cuda.synchronize()
+    t_init0 = time.perf_counter()
     ctx = E.eaadc_init(o, v, naux, pr["eps_occ"], pr["eps_vir"], pr["B"], local, sh)
     try:
         E.eaadc_build_canonical(ctx, 3, 1.0)
+        torch.cuda.synchronize()
+        init_build_fp64_s = time.perf_counter() - t_init0
         _, _, dim = E.eaadc_state_info(ctx, 0)
         nvec = NROOTS
         x = torch.randn(nvec, dim, dtype=torch.float64, device="cuda")
@@ -385,6 +419,8 @@ def main():
         }
         if roots is not None:
             line["time_to_roots"] = roots
+        if roots is not None and "fp64_gpu" in roots:
+            line["end_to_end"] = end_to_end(E, pr, local, sh, init_build_fp64_s, roots["fp64_gpu"]["seconds"])
         if not args.no_fno and rank == 0:
             line["fno_states"] = fno_states(E, ctx)
         if rank == 0 and world == 1:

@@ -188,6 +188,15 @@ eaadc_status eaadc_ladder_noalloc(eaadc_ctx* ctx, int state, int nvec, const dou
  * 1p part, e_b + e_c - e_k for the 2p1h part. */
 eaadc_status eaadc_diagonal(eaadc_ctx* ctx, int state, double* diag_host);
 
+/* Precision of the pp-ladder of the first-order amplitudes inside M^(3)
+ * (sum_Q B^Q tau_ij B^Q over the o^2 pairs, 4 o^2 v^3 naux flop: the largest
+ * cost of building a state) for the states built next by
+ * eaadc_build_canonical or eaadc_build_states: EAADC_FP64 (the default), or
+ * the tensor-core ladder in EAADC_MIXED_BF16 or EAADC_MIXED_BF16X3 (about
+ * 1e-5 relative; the state's reduced-precision operands are made then too).
+ * Everything else in the build stays FP64. */
+eaadc_status eaadc_set_build_precision(eaadc_ctx* ctx, int prec);
+
 /* Per-state truncated spaces (Sec. II.C-E; the algorithm of Sec. III),
  * replacing any states built before.  Solves the canonical EA-ADC(2) problem
  * for its nstates lowest roots (FP64 Davidson with can_opts, or tol 1e-8,

@@ -30,7 +30,7 @@ EXPORTED = (
     "eaadc_destroy", "eaadc_last_error", "eaadc_ladder", "eaadc_kernel_launches",
     "eaadc_ladder_noalloc", "eaadc_build_states", "eaadc_ea_energies", "eaadc_eigh_sym", "eaadc_num_states",
     "eaadc_precond_load", "eaadc_precond_get", "eaadc_precond_pairs", "eaadc_mlp_forward", "eaadc_mlp_loss_grad",
-    "eaadc_mlp_train_step", "eaadc_get_trace",
+    "eaadc_mlp_train_step", "eaadc_get_trace", "eaadc_set_build_precision",
 )
 MLP_FEATURES = 16
 MLP_PARAMS = 136193
@@ -79,6 +79,7 @@ def lib():
         L.eaadc_mlp_loss_grad.argtypes = [vp, C.c_int, ip, vp, vp, vp, vp, dp, fp, vp]
         L.eaadc_mlp_train_step.argtypes = [vp, C.c_int, ip, vp, vp, vp, vp, C.c_float, dp, vp]
         L.eaadc_get_trace.argtypes = [vp, C.c_int, ip, ip, dp, dp, dp]
+        L.eaadc_set_build_precision.argtypes = [vp, C.c_int]
         L.eaadc_num_states.restype = C.c_int
         L.eaadc_get_m11.argtypes = [vp, C.c_int, dp]
         L.eaadc_davidson.argtypes = [vp, C.c_int, C.POINTER(DavidsonOpts), dp, dp, ip]
@@ -165,6 +166,11 @@ def eaadc_ladder_noalloc(ctx, state, nvec, x_ptr, out_ptr, stream=None):
     """As eaadc_ladder, working in the library's fixed device array instead of
     allocating (for callers that cannot allocate device memory mid-run)."""
     _check(ctx, lib().eaadc_ladder_noalloc(ctx, state, nvec, C.c_void_p(x_ptr), C.c_void_p(out_ptr), stream))
+
+
+def eaadc_set_build_precision(ctx, prec):
+    """Precision of the amplitude ladder in the next state builds (EAADC_FP64 default)."""
+    _check(ctx, lib().eaadc_set_build_precision(ctx, prec))
 
 
 def eaadc_build_states(ctx, nstates, fno_thresh, naf_thresh, adc_order=3, x3=1.0, can_opts=None):

@@ -113,7 +113,7 @@ eaadc_status eaadc_build_canonical(eaadc_ctx* ctx, int adc_order, double x3) {
     auto* st = new ea::State();
     ctx->states.push_back(st);
     st->o = ctx->o; st->v = ctx->v; st->naux = ctx->naux;
-    st->order = adc_order; st->x3 = x3;
+    st->order = adc_order; st->x3 = x3; st->build_prec = ctx->build_prec;
     const int o = ctx->o, v = ctx->v, naux = ctx->naux;
     st->eo.alloc(o, s); st->ev.alloc(v, s);
     st->Boo.alloc((size_t)naux * o * o, s);
@@ -142,6 +142,15 @@ eaadc_davidson_opts inner_opts(const eaadc_davidson_opts* o) {
   return d;
 }
 }  // namespace
+
+eaadc_status eaadc_set_build_precision(eaadc_ctx* ctx, int prec) {
+  if (!ctx) return EAADC_ERR_ARG;
+  return guarded(ctx, [&] {
+    if (prec != EAADC_FP64 && prec != EAADC_MIXED_BF16 && prec != EAADC_MIXED_BF16X3)
+      ea::fail(EAADC_ERR_ARG, "unknown precision");
+    ctx->build_prec = prec;
+  });
+}
 
 eaadc_status eaadc_build_states(eaadc_ctx* ctx, int nstates, const double* fno_thresh, const double* naf_thresh,
                                 int adc_order, double x3, const eaadc_davidson_opts* can_opts) {

@@ -177,7 +177,7 @@ void build_fno_states(eaadc_ctx* ctx, int nstates, const double* fno_thr, const 
       // 6. the truncated state
       State* st = new State();
       built.push_back(st);
-      st->o = o; st->v = vp; st->naux = np; st->order = order; st->x3 = x3;
+      st->o = o; st->v = vp; st->naux = np; st->order = order; st->x3 = x3; st->build_prec = ctx->build_prec;
       st->vfull = v; st->nauxfull = naux; st->omega2_can = w2c[k];
       copy_d(s, st->eo, ctx->eo.p, o);
       st->ev = std::move(efno);

@@ -150,7 +150,10 @@ void build_state_intermediates(eaadc_ctx* ctx, State& st) {
   if (st.order >= 3 && st.x3 != 0.0) {
     // second-order doubles: pp-ladder, hh-ladder, ring terms
     DArr<double> lad((size_t)(oo * vv), s);
-    ladder_fp64(s, st.Bvv.p, naux, v, st.tau.p, vv, 1, 0, (int)oo, lad.p, 0, vv, 1.0, 0.0);
+    if (st.build_prec == EAADC_FP64)
+      ladder_fp64(s, st.Bvv.p, naux, v, st.tau.p, vv, 1, 0, (int)oo, lad.p, 0, vv, 1.0, 0.0);
+    else  // tensor cores; the intermediates above are what the operand copies need
+      ladder_pairs_tc(s, st, st.tau.p, (int)oo, st.build_prec == EAADC_MIXED_BF16X3, lad.p);
     DArr<double> oooo((size_t)(oo * oo), s), ooov((size_t)(oo * ov), s);
     dgemm(s, true, false, (int)oo, (int)oo, naux, 1.0, st.Boo.p, oo, st.Boo.p, oo, 0.0, oooo.p, oo);
     dgemm(s, true, false, (int)oo, (int)ov, naux, 1.0, st.Boo.p, oo, st.Bov.p, ov, 0.0, ooov.p, ov);

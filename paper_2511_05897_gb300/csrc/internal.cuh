@@ -141,6 +141,7 @@ struct State {
   long long dim = 0;
   int order = 3;
   double x3 = 1.0;
+  int build_prec = EAADC_FP64;  // precision of the pp-ladder of the amplitudes in M^(3)
   DArr<double> eo, ev;            // [o], [v]
   DArr<double> Boo, Bov, Bvv;     // [naux][o][o], [naux][o][v], [naux][v][v]
   DArr<double> tau;               // [o][o][v][v]  (ia|jb)/D
@@ -203,12 +204,16 @@ struct eaadc_ctx {
   ea::DArr<double> eo, ev, Boo, Bov, Bvv;
   std::vector<ea::State*> states;
   ea::Mlp mlp;
+  int build_prec = EAADC_FP64;  // for the states built next (eaadc_set_build_precision)
   std::string err;
   ~eaadc_ctx();
 };
 
 namespace ea {
 void build_state_intermediates(eaadc_ctx* ctx, State& st);
+// out[m] (FP64 [v][v], stride v*v) = sum_Q B^Q T[m] B^Q for nmat matrices T
+// (FP64 [v][v]) on the tensor cores (BF16, or split BF16 when x3).
+void ladder_pairs_tc(cudaStream_t s, State& st, const double* T, int nmat, bool x3, double* out);
 void sigma_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y);
 void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y, bool x3);
 void sigma_base_fp64(cudaStream_t s, State& st, int nvec, const double* x, double* y, bool ring, bool ladder);

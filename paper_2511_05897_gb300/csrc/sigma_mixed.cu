@@ -396,6 +396,22 @@ void couple21_nv(cudaStream_t s, const CoupOps<float>& c, const float* V, int nv
   einsumT<float>(s, "Qla,Qnl->an", 1.f, Bov, ttt, 1.f, syt);
 }
 
+// W[(m,c)][d] (pitch in W) = T[m][c][d], hi/lo BF16 split when W.lo
+__global__ void pack_mats_bf16(const double* __restrict__ T, OpDst W, long long total, int v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x)
+    put(W, i / v, i % v, T[i]);
+}
+
+// out[m][b][c] = L[(m,c)][b] (row pitch lp): the ladder output is transposed
+__global__ void unpack_ladder(const float* __restrict__ L, long long lp, double* __restrict__ out, long long total,
+                              int v) {
+  const long long vv = (long long)v * v;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const long long m = i / vv, b = (i / v) % v, c = i % v;
+    out[i] = (double)L[(m * v + c) * lp + b];
+  }
+}
+
 // compact out[r][c] (pitch v) = in[r][c] (pitch ip)
 __global__ void compact_f32(const float* __restrict__ in, long long ip, float* __restrict__ out, long long rows, int v) {
   long long n = rows * v;
@@ -430,14 +446,21 @@ static void ladder_run(cudaStream_t s, State& st, const bf16* Wbf, const bf16* W
 // then the pipeline variants of each stage at the best chunk size, with CUDA
 // events on the stream (every run producing the full ladder in out), and
 // keeps the fastest plan.
+void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out, long long op,
+               bool tune = true);
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, bool>, LadderPlan> g_ladder_plan;
 
-void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out, long long op) {
+void ladder_tc(cudaStream_t s, State& st, const bf16* Wbf, const bf16* Wlo, int nmat, float* out, long long op,
+               bool tune) {
   const int v = st.v, naux = st.naux;
   const bool x3 = Wlo != nullptr;
   const long long per_q = std::max<long long>(1, (long long)nmat * v * pad8(v));
   auto qc_of = [&](long long budget) { return (int)std::min<long long>(naux, std::max<long long>(1, budget / per_q)); };
+  if (!tune) {  // one-off use: the default plan (Z about 48 M elements, split mode 24 M)
+    ladder_run(s, st, Wbf, Wlo, nmat, out, op, LadderPlan{qc_of(x3 ? 24LL << 20 : 48LL << 20), 0, 0});
+    return;
+  }
   const auto key = std::make_tuple(v, naux, nmat, x3);
   LadderPlan plan{-1, 0, 0};
   {
@@ -546,6 +569,20 @@ static void ladder_run(cudaStream_t s, State& st, const bf16* Wbf, const bf16* W
       gemm_split(s, mZ, &mZl, mBb, &mBbl, mOut, g2);
     }
   }
+}
+
+void ladder_pairs_tc(cudaStream_t s, State& st, const double* T, int nmat, bool x3, double* out) {
+  const int v = st.v;
+  const long long wp = rp64(v), lp = rp32(v), total = (long long)nmat * v * v;
+  prepare_mixed(s, st, x3);
+  DArr<bf16> W((size_t)(nmat * v * wp), s), Wl;
+  if (x3) Wl.alloc(W.n, s);
+  pack_mats_bf16<<<gridn(total), 256, 0, s>>>(T, OpDst{W.p, wp, x3 ? Wl.p : nullptr}, total, v);
+  EA_LAUNCH();
+  DArr<float> L((size_t)(nmat * v * lp), s);
+  ladder_tc(s, st, W.p, x3 ? Wl.p : nullptr, nmat, L.p, lp, false);
+  unpack_ladder<<<gridn(total), 256, 0, s>>>(L.p, lp, out, total, v);
+  EA_LAUNCH();
 }
 
 void sigma_mixed(cudaStream_t s, State& st, int nvec, const double* x, double* y, bool x3) {

@@ -224,3 +224,45 @@ def test_canonical_200_mixed_refined_against_oracle(E, prec):
         assert np.abs(om[0] - g["omega3"]).max() <= 1e-8
     finally:
         E.eaadc_destroy(ctx)
+
+
+@pytest.mark.parametrize("o,v,naux,decay,seed", [(4, 13, 40, 8.0, 9), (3, 136, 90, 20.0, 7)])
+def test_tensor_core_build_of_m11(E, o, v, naux, decay, seed):
+    """M^(3) with its amplitude ladder on the tensor cores (split BF16) against
+    the FP64 build: the ladder term carries ~1e-5 relative error, held to
+    1e-4 of max |M_ab| and 1e-6 Eh in the roots."""
+    pr = make_problem(o, v, naux, decay, seed)
+    ctx = E.eaadc_init(o, v, naux, pr["eps_occ"], pr["eps_vir"], pr["B"], 0)
+    try:
+        E.eaadc_build_canonical(ctx, 3, 1.0)
+        m64 = E.eaadc_get_m11(ctx, 0)
+        w64 = E.eaadc_davidson(ctx, 3, tol=1e-8)[0][0]
+        E.eaadc_set_build_precision(ctx, E.EAADC_MIXED_BF16X3)
+        E.eaadc_build_canonical(ctx, 3, 1.0)
+        mx = E.eaadc_get_m11(ctx, 0)
+        wx = E.eaadc_davidson(ctx, 3, tol=1e-8)[0][0]
+        print(f"tensor-core build: M11 rel err {np.abs(mx - m64).max() / np.abs(m64).max():.1e}, "
+              f"roots {np.abs(wx - w64).max():.1e} Eh")
+        assert np.abs(mx - m64).max() <= 1e-4 * np.abs(m64).max()
+        assert np.abs(wx - w64).max() <= 1e-6
+    finally:
+        E.eaadc_destroy(ctx)
+
+
+@pytest.mark.skipif(not os.path.exists(os.path.join(GOLD, "canonical-200.npz")), reason="golden file missing")
+def test_canonical_200_tensor_core_build_against_oracle(E):
+    """Whole reduced-precision pipeline: split-BF16 amplitude ladder in the
+    build, BF16 Davidson, FP64 Ritz step: roots within 1e-5 Eh of the oracle."""
+    g = np.load(os.path.join(GOLD, "canonical-200.npz"))
+    pr = config_problem("canonical-200")
+    ctx = E.eaadc_init(pr["o"], pr["v"], pr["naux"], pr["eps_occ"], pr["eps_vir"], pr["B"], 0)
+    try:
+        E.eaadc_set_build_precision(ctx, E.EAADC_MIXED_BF16X3)
+        E.eaadc_build_canonical(ctx, 3, 1.0)
+        m11 = E.eaadc_get_m11(ctx, 0)
+        assert np.abs(m11 - g["m11_3"]).max() <= 1e-4 * np.abs(g["m11_3"]).max()
+        om, rn, it, st = E.eaadc_davidson(ctx, 4, tol=1e-5, prec=E.EAADC_MIXED_BF16, refine=2, max_sub=40, maxit=300)
+        print(f"tensor-core build, BF16 Davidson + FP64 Ritz: max err {np.abs(om[0] - g['omega3']).max():.1e} Eh")
+        assert np.abs(om[0] - g["omega3"]).max() <= 1e-5
+    finally:
+        E.eaadc_destroy(ctx)
