@@ -267,3 +267,21 @@ def test_p9_mp2_density_is_second_order_exact_density():
     Dmp2 = fno.mp2_density(p)
     assert np.abs(Dmp2).max() > 1e-5
     assert np.abs(D2 - Dmp2).max() < 1e-10 * max(1.0, np.abs(Dmp2).max())
+
+
+# ---------------------------------------------------------------------- R13
+def test_r13_sm_scale_multiplies_third_order_block_only():
+    """sm-ADC reading: x scales M^(3)_ab only. With x = 0 the 1p/1p block is
+    the second-order one, the second-order coupling and the first-order
+    2p1h block stay; x is linear in the 1p/1p block."""
+    pr = _tiny(2, 3, 8, 4.0, 6)
+    p = R.Problem(pr["eps_occ"], pr["eps_vir"], pr["B"])
+    v = p.v
+    M3 = R.explicit_matrix(p, 3, 1.0)
+    M0 = R.explicit_matrix(p, 3, 0.0)
+    Mh = R.explicit_matrix(p, 3, 0.5)
+    M2 = R.explicit_matrix(p, 2)
+    assert np.abs(M0[:v, :v] - M2[:v, :v]).max() < 1e-14
+    assert np.abs(M0[v:, :] - M3[v:, :]).max() < 1e-14          # coupling and 2p1h block unchanged
+    assert np.abs(M0[v:, :v] - M2[v:, :v]).max() > 1e-6          # C^(2) kept, not ADC(2)
+    assert np.abs(Mh[:v, :v] - 0.5 * (M0[:v, :v] + M3[:v, :v])).max() < 1e-14
