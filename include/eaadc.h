@@ -20,6 +20,11 @@
  *    device memory is owned by the context and freed by eaadc_destroy.
  *  - A context is bound to one CUDA device; calls on one context must not run
  *    concurrently (thread-compatible, not thread-safe).
+ *  - Device memory is taken from the stream-ordered allocator on the stream
+ *    of the call; state buffers made during a call (the reduced-precision
+ *    operand copies on the first such call, the learned-correction feature
+ *    table) stay with the context and are released on that stream by
+ *    eaadc_destroy: a stream passed to a call must outlive the context.
  *  - Vector layout of one attached-state vector of state s (dimension
  *    dim = v' + o*v'*v'): [1p part y[a], a < v'] followed by the 2p1h part
  *    w[k][b][c] (k < o, b, c < v', c fastest) in the orthonormal doublet
