@@ -1,13 +1,14 @@
 // Mixed-precision sigma: every o v^3-scaling contraction runs on tcgen05
-// tensor cores with BF16 operands and FP32 accumulation; the orbital-energy
-// diagonal, the 1p/1p block and the DF contractions that scale as
-// naux * o * v^2 stay in FP64.
+// tensor cores with BF16 operands and FP32 accumulation; the DF coupling
+// contractions that scale as naux * o * v^2 run in FP32 on CUDA cores, batched
+// over the vectors; the orbital-energy diagonal and the 1p/1p block stay FP64.
 //
 // Ladder (Sec. II.B: four-virtual integrals are never formed; (bd|ce) enters
 // as two DF contractions):
 //   stage 1  Z[(nk,c)][(Q,d)] = sum_e B^Q[c][e] W_nk[d][e]
 //   stage 2  L[(nk,c)][b]     = sum_(Q,d) Z[(nk,c)][(Q,d)] B^Q[b][d] = (sum_Q B^Q W_nk B^Q)[b][c]
-// in chunks of qc auxiliary functions (BF16 intermediate Z about 96 MB);
+// in chunks of qc auxiliary functions (BF16 intermediate Z of 12-96 MB, the
+// chunk size and GEMM pipeline shapes picked per shape by ladder_tc's tuner);
 // stage 2 is one GEMM over all pair matrices nk, accumulated over chunks by
 // TMA reduce-add.
 // Ring and coupling: sigma_A = -T1[(k,b),(n,c)] - T2[(k,c),(n,b)] with
@@ -139,9 +140,10 @@ __global__ void fg_operands(const float* __restrict__ F, const float* __restrict
   }
 }
 
-// FP64 per-vector H tensors from the tensor-core outputs (rows (l,d), columns (n,x)):
-//   H1_n[l][d][c] = H1[(l,d)][(n,c)]
-//   H2_n[b][l][d] = H23[(l,d)][(n,b)]        H3_n[l][b][d] = H23[ov + (l,d)][(n,b)]
+// FP32 per-vector H tensors for the coupling pieces, from the tensor-core
+// outputs (rows (l,d), columns (n,x)):
+//   h1[n][l][c][d] = H1[(l,d)][(n,c)]   (that is H1_n[l][d][c])
+//   h2[n][b][l][d] = H23[(l,d)][(n,b)]        h3[n][l][b][d] = H23[ov + (l,d)][(n,b)]
 __global__ void h_from_tc(const float* __restrict__ H1, const float* __restrict__ H23, float* __restrict__ h1,
                           float* __restrict__ h2, float* __restrict__ h3, int nvec, int o, int v, long long nv) {
   const long long ov = (long long)o * v, n2 = ov * v;
