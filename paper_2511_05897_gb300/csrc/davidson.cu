@@ -11,6 +11,13 @@
 // themselves by canonical orthogonalisation (eigenvectors of their Gram
 // matrix, directions with eigenvalue <= 1e-18 dropped); the subspace restarts
 // from the 2*nroots lowest Ritz vectors when it would exceed max_sub.
+//
+// Options: a reduced-precision sigma (the phase also stops at its noise
+// floor) followed by FP64 iterations or by one sigma-and-Ritz step in FP64 or
+// split BF16; the learned correction of precond.cu with a per-root fallback
+// to the diagonal one; a trace of the first iterates (training pairs).
+// Subspace updates and Gram products are bandwidth-bound kernels that read
+// each basis vector once per call.
 #include "internal.cuh"
 
 #include <algorithm>
